@@ -1,0 +1,326 @@
+"""Benchmark of the GB300 Louvain+ hot path (local-move passes + contraction).
+
+One step = one full Louvain+ clustering (Algorithm 1: every coarsening and
+uncoarsening level, all local-move passes, every contraction) of one seeded
+synthetic graph whose CSR is resident in HBM when the timed region starts.
+
+Default workload: R-MAT scale 22 (4,194,304 vertices, edge factor 16,
+a,b,c,d = .57/.19/.19/.05), symmetrised, deduplicated, loops removed, int32
+weights uniform in [1,8], modularity (w(v) = weighted degree,
+lambda = 1/sum of edge weights).  value = stored edges (nnz = 2m, the
+paper's 2m/t rate) per second of device time, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload rmat22|grid256|sbm10k] [--no-cpu-baseline]
+
+Multi-GPU: one process per GPU under torchrun; a single graph does not
+shard, so each rank clusters its own replica (weak scaling, no collective on
+the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "local-move+contraction edges/s, e2e time; batched/served graphs/s, p99 vs plain"
+
+WORKLOADS = {
+    "rmat22": dict(desc="R-MAT scale 22, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), symmetrised, "
+                        "dedup, no loops, int32 weights U[1,8], modularity, int32 indices", ),
+    "grid256": dict(desc="3-D 7-point grid 256^3, 1% of edges rewired, int32 weights U[1,16], unit vertex "
+                         "weights, CPM lambda=1/100"),
+    "sbm10k": dict(desc="planted-partition SBM, 10,000 vertices in 100 blocks, p_in .05, p_out .0005, "
+                        "unit weights, modularity, seed 0"),
+}
+
+
+def make_graph(name: str, scale_override: int | None = None):
+    import graphgen as gg
+
+    if name == "rmat22":
+        return gg.rmat(scale_override or 22, 16, seed=1, wmax=8)
+    if name == "grid256":
+        return gg.grid_cpm(side=scale_override or 256)
+    if name == "sbm10k":
+        return gg.sbm_planted()
+    raise ValueError(name)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(workload: str, budget_s: float = 20.0):
+    """The CPU oracle (single thread, as it stands) on a bounded sample of the
+    workload family, reported in the metric's unit."""
+    import graphgen as gg
+    import oracle
+
+    if workload == "rmat22":
+        scale = 18
+        g = gg.rmat(scale, 16, seed=1, wmax=8)
+        sample = f"full Louvain+ on R-MAT scale {scale} (same generator, edge factor, weights, objective)"
+    elif workload == "grid256":
+        g = gg.grid_cpm(side=64)
+        sample = "full Louvain+ on the 64^3 grid of the same recipe (CPM 1/100)"
+    else:
+        g = gg.sbm_planted()
+        sample = "full Louvain+ on the same SBM graph"
+    runs, t_total = 0, 0.0
+    while t_total < budget_s and runs < 5:
+        t0 = time.perf_counter()
+        oracle.louvain_plus(g)
+        t_total += time.perf_counter() - t0
+        runs += 1
+    return {"value": g.nnz * runs / t_total, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": sample + f"; {runs} run(s), {t_total:.1f} s; nnz={g.nnz}"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle timed as it stands on the host cores."""
+    if rank != 0:
+        return
+    import graphgen as gg
+    import oracle
+
+    if args.workload == "rmat22":
+        g = gg.rmat(17, 16, seed=1, wmax=8)
+        sample = "R-MAT scale 17 sample of the workload (same recipe)"
+    elif args.workload == "grid256":
+        g = gg.grid_cpm(side=48)
+        sample = "48^3 grid sample of the workload (same recipe)"
+    else:
+        g = gg.sbm_planted()
+        sample = "the SBM graph itself"
+    for _ in range(args.warmup):
+        oracle.louvain_plus(g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.louvain_plus(g)
+    dt = time.perf_counter() - t0
+    value = g.nnz * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
+                       "sample": sample, "nnz": g.nnz},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--scale", type=int, default=None, help="override the size (R-MAT scale / grid side)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import paper_2608_01503_gb300 as lc
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+
+        dist = dist_
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    g = make_graph(args.workload, args.scale)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, col, ew, vw = t(g.row_ptr), t(g.col), t(g.ew), t(g.vw)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts_prof = lc.Options(profile=True)
+
+    res = None
+    for _ in range(args.warmup):
+        _, res = lc.lc_cluster(rp, col, ew, vw, g.lam_num, g.lam_den, opts=opts_prof, labels_out=labels)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms = {k: 0.0 for k in lc.LC_K_NAMES}
+    kbytes = {k: 0.0 for k in lc.LC_K_NAMES}
+    klaunch = {k: 0 for k in lc.LC_K_NAMES}
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, res = lc.lc_cluster(rp, col, ew, vw, g.lam_num, g.lam_den, opts=opts_prof, labels_out=labels)
+        for k in lc.LC_K_NAMES:
+            kms[k] += res["kernel_ms"][k]
+            kbytes[k] += res["kernel_bytes"][k]
+            klaunch[k] += res["kernel_launches"][k]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    value = g.nnz * world / (ms_step / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_rp, h_col, h_ew, h_vw = pin(g.row_ptr), pin(g.col), pin(g.ew), pin(g.vw)
+        h_lab = torch.empty(g.n, dtype=torch.int32).pin_memory().numpy()
+        lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab)
+        k2 = max(1, min(args.steps, 5))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab)
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / k2
+        if dist:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": g.nnz * world / e2e_s, "unit": "edges/s", "seconds_per_step": e2e_s,
+               "h2d_bytes_per_step": int(h_rp.nbytes + h_col.nbytes + h_ew.nbytes + h_vw.nbytes),
+               "d2h_bytes_per_step": int(4 * g.n)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    dom = max(lc.LC_K_NAMES, key=lambda k: kms[k])
+    achieved = kbytes[dom] / (kms[dom] / 1000.0) / 1e9 if kms[dom] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (hbm_gbs)",
+                "traffic": None, "launches": klaunch[dom],
+                "algorithmic_bytes_per_step": kbytes[dom] / args.steps}
+    breakdown = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
+                     "algorithmic_GBps": (kbytes[k] / (kms[k] / 1000.0) / 1e9) if kms[k] > 0 else None}
+                 for k in lc.LC_K_NAMES}
+    lm_ms = (kms["first_pass"] + kms["move"] + kms["afterburner"] + kms["apply"] + kms["objective"]) / args.steps
+    ct_ms = kms["contract"] / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
+                   "n": g.n, "nnz": g.nnz, "edges_counted": "nnz = 2m (both directions), the paper's 2m/t",
+                   "l2": "inputs larger than L2 (CSR > 129 MB); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "result": {"n_clusters": res["n_clusters"], "levels": res["levels"],
+                   "passes": res["passes_total"], "modularity": res["modularity"], "phi": res["phi"]},
+        "local_move_edges_per_s": res["edges_local_move"] / (lm_ms / 1000.0) if lm_ms > 0 else None,
+        "contraction_edges_per_s": res["edges_contract"] / (ct_ms / 1000.0) if ct_ms > 0 else None,
+        "breakdown": breakdown,
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(sum(klaunch.values())),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * lc.h — C ABI of the GB300 (sm_103a) pLouvain / Louvain+ library, liblc.so.
+ *
+ * The library clusters an undirected graph by optimising the LambdaCC
+ * objective (Gilbert & Madduri, "GPU-Accelerated Multilevel Graph Clustering:
+ * A Parallel Perspective on Louvain and Leiden", Section II-A, Eq. 1):
+ *
+ *   lambdaCC(C) = sum over clusters C_i, over ordered pairs u != v in C_i,
+ *                 of ( w(u,v) - lambda * w(u) * w(v) )
+ *
+ * with positive integer vertex weights w(v), positive integer edge weights
+ * w(u,v) and a rational lambda = lambda_num / lambda_den in [0, 1].
+ * Modularity is the special case w(v) = weighted degree and
+ * lambda = gamma / (sum of all stored edge weights); the Constant Potts
+ * Model is w(v) = 1 (Section II-A).
+ *
+ * The method is Louvain+ (Algorithm 1): coarsening levels of synchronous
+ * local-move passes (Algorithm 2) filtered by the afterburner (Algorithm 3),
+ * gather-free graph contraction (Algorithm 4), then uncoarsening levels that
+ * project and re-run the local-move passes.  All arithmetic is exact integer;
+ * results are deterministic and independent of thread scheduling.
+ *
+ * Conventions shared by every entry point:
+ *  - Graphs are CSR: row_ptr int64[n+1] (row_ptr[0] = 0, row_ptr[n] = nnz,
+ *    non-decreasing), col int32[nnz] in [0, n), edge weights int32[nnz] > 0.
+ *    Both directions of every undirected edge are stored with equal weight;
+ *    rows are strictly increasing (sorted, no duplicates); no self-loops.
+ *  - Vertex weights int64[n] >= 0 (Section II asks for positive weights; zero
+ *    is also accepted, the modularity weight of an isolated vertex).
+ *    0 <= lambda_num <= lambda_den, lambda_den > 0.
+ *  - Unless an entry point says "host", every pointer argument that refers
+ *    to graph or label data is DEVICE memory on the current CUDA device,
+ *    owned by the caller, read-only unless it is an output, and not retained
+ *    after the call returns.  Work is issued on opts->stream (NULL = the
+ *    legacy default stream); every call returns after its results are
+ *    complete on that stream (calls read per-level sizes back to the host).
+ *  - Scratch device memory is taken from CUDA's stream-ordered allocator
+ *    (cudaMallocAsync on opts->stream) and released before return.
+ *  - Return value: LC_OK or an LC_ERR_* code; on error no output is
+ *    guaranteed to have been written (labels_out may hold partial data) and
+ *    *res is zeroed except for res->error_detail.  lc_strerror() names it.
+ *  - Exactness guards (checked before any work, LC_ERR_OVERFLOW):
+ *    T = sum of edge weights < 2^31 and, with V = sum of vertex weights,
+ *    B = lambda_den*T + lambda_num*V^2 < 2^60, and
+ *    (eps_den/eps_num) * 2 * (T + lambda_num*V^2/lambda_den) < 2^60.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LC_API __attribute__((visibility("default")))
+#else
+#define LC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LC_OK = 0,
+  LC_ERR_ARG = 1,        /* bad argument, size or option */
+  LC_ERR_ASYMMETRIC = 2, /* some (u,v,w) has no matching (v,u,w) */
+  LC_ERR_SELF_LOOP = 3,  /* some row v lists v */
+  LC_ERR_DUPLICATE = 4,  /* a row is not strictly increasing */
+  LC_ERR_WEIGHT = 5,     /* an edge weight <= 0 or a vertex weight < 0 */
+  LC_ERR_OVERFLOW = 6,   /* exactness guard tripped (see above) */
+  LC_ERR_OOM = 7,        /* device allocation failed */
+  LC_ERR_CUDA = 8,       /* a CUDA runtime call failed */
+  LC_ERR_TIMEOUT = 9,    /* level cap (256) reached */
+  LC_ERR_DEVICE = 10,    /* a kernel reported an internal bound violation */
+  LC_ERR_NOT_READY = 11  /* server: job still running */
+};
+
+/* Graph topology: n vertices, nnz stored (directed) entries. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t *row_ptr; /* [n+1] */
+  const int32_t *col;     /* [nnz] */
+} lc_csr;
+
+/* Trace record delivered to lc_opts.event_cb (host copies, valid during the
+ * callback only).  Used to compare every pass and level with a reference. */
+enum { LC_EV_PASS = 1, LC_EV_LMP = 2, LC_EV_CONTRACT = 3 };
+typedef struct {
+  int32_t kind;   /* LC_EV_* */
+  int32_t level;  /* graph level l (0 = input) */
+  int32_t phase;  /* 0 coarsening, 1 uncoarsening */
+  int32_t pass;   /* 1-based pass index (PASS only) */
+  int64_t n;      /* vertices of G_l */
+  const int32_t *labels; /* PASS: C after the pass; LMP: C_out; CONTRACT: dense C */
+  const int32_t *dest;   /* PASS: D[v] for candidates, -1 non-candidate, -2 empty cluster */
+  const uint8_t *moved;  /* PASS: 1 if v passed the afterburner */
+  int64_t phi;           /* PASS: Phi(C after pass); LMP: Phi(C_out) (Phi = lambda_den*lambdaCC) */
+  int64_t count_L, count_M;
+  int64_t cn, cnnz;      /* CONTRACT: coarse graph G_{l+1} (rows unsorted) */
+  const int64_t *c_row_ptr;
+  const int32_t *c_col;
+  const int32_t *c_ew;
+  const int64_t *c_vw;
+} lc_event;
+typedef void (*lc_event_fn)(void *ctx, const lc_event *ev);
+
+/* Options.  Initialise with lc_default_opts(). */
+typedef struct {
+  int32_t pass_limit;       /* passes per LocalMovePasses call (Algorithm 2); default 6, max 16 */
+  int32_t phi_num[16];      /* temperature phi_i = phi_num[i]/phi_den[i] of pass i+1 */
+  int32_t phi_den[16];      /* default 3/4 for passes 1-4, 1/4 for passes 5-6 (Section VI-C) */
+  int32_t eps_num, eps_den; /* epsilon of the afterburner ordering (Section IV-A-1); default 1/10 */
+  uint32_t seed;            /* salt of the ordering hash; default 0 */
+  int32_t uncoarsen;        /* 1 = Louvain+ (default), 0 = Louvain (Algorithm 1 line 12 off) */
+  int32_t validate;         /* 1 = check the CSR preconditions on the device (default) */
+  int32_t profile;          /* 1 = time each kernel class with CUDA events into lc_result */
+  void *stream;             /* cudaStream_t */
+  lc_event_fn event_cb;     /* optional per-pass / per-level trace (slow: syncs and copies) */
+  void *event_ctx;
+} lc_opts;
+
+/* Kernel classes timed when opts.profile = 1. */
+enum {
+  LC_K_FIRST_PASS = 0, /* first-pass argmax straight from the CSR (Section IV-A-3) */
+  LC_K_MOVE = 1,       /* neighbour-cluster aggregation + gain argmax + candidate test */
+  LC_K_AFTERBURNER = 2,
+  LC_K_APPLY = 3,      /* update + new-singleton ids + best-of copy */
+  LC_K_OBJECTIVE = 4,
+  LC_K_CONTRACT = 5,   /* label compaction + contraction */
+  LC_K_OTHER = 6,      /* binning, projection, validation, guards */
+  LC_K_COUNT = 7
+};
+
+typedef struct {
+  int64_t n_clusters;
+  int32_t levels;       /* number of graphs G_0..G_top */
+  int32_t passes_total; /* local-move passes run, all levels and phases */
+  int64_t phi;          /* exact Phi = lambda_den * lambdaCC(labels) */
+  int64_t lambda_den;
+  double objective;     /* lambdaCC = phi / lambda_den */
+  double modularity;    /* (phi - lambda_num*sum w(v)^2) / (lambda_den * sum w(u,v));
+                           the modularity when w(v) is the weighted degree */
+  int64_t edges_local_move; /* sum over passes of nnz(G_l) */
+  int64_t edges_contract;   /* sum over contractions of nnz(G_l) */
+  /* opts.profile = 1: per kernel class, total milliseconds, launches and
+   * algorithmic bytes (the minimum bytes the kernels must move) */
+  double kernel_ms[LC_K_COUNT];
+  int64_t kernel_launches[LC_K_COUNT];
+  double kernel_bytes[LC_K_COUNT];
+  int64_t error_detail; /* extra context for some errors (e.g. offending vertex) */
+} lc_result;
+
+/* Fill *o with the defaults of Section VI-C (pass limit 6, phi 3/4 x4 then
+ * 1/4 x2, epsilon 1/10, seed 0, Louvain+, validate on, profile off). */
+LC_API void lc_default_opts(lc_opts *o);
+
+/* Human-readable name of an LC_* code (static string). */
+LC_API const char *lc_strerror(int code);
+
+/* Louvain+ (Algorithm 1) on G = (g, vertex_w, edge_w) with
+ * lambda = lambda_num / lambda_den.  labels_out: device int32[n], written
+ * with dense cluster ids 0..k-1 numbered in ascending order of the level-0
+ * cluster id.  res (host) receives counts, the exact objective and, with
+ * opts.profile, kernel timings.  opts may be NULL for the defaults. */
+LC_API int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
+               int64_t lambda_den, const lc_opts *opts, int32_t *labels_out, lc_result *res);
+
+/* Same as lc_cluster with HOST buffers (pinned or pageable): copies the graph
+ * to the device on opts->stream, clusters it, and copies labels_out (host
+ * int32[n]) back before returning. */
+LC_API int lc_cluster_host(const lc_csr *g_host, const int64_t *vertex_w, const int32_t *edge_w,
+                    int64_t lambda_num, int64_t lambda_den, const lc_opts *opts,
+                    int32_t *labels_out, lc_result *res);
+
+/* One LocalMovePasses call (Algorithm 2 with Algorithm 3) from the device
+ * clustering labels_inout (int32[n], values in [0, n)), which is replaced by
+ * the best clustering seen (C_out).  singleton_start = 1 asserts that the
+ * input is the all-singleton clustering labels[v] = v, enabling the
+ * first-pass shortcut of Section IV-A-3 (the result is the same). */
+LC_API int lc_local_move(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                  int64_t lambda_num, int64_t lambda_den, const lc_opts *opts,
+                  int32_t *labels_inout, int32_t singleton_start, lc_result *res);
+
+/* Graph contraction (Algorithm 4; the coarse graph of Section III-A): labels
+ * is a device int32[n] clustering with dense ids in [0, n_c).  Writes the
+ * coarse graph into caller-allocated device buffers: c_row_ptr int64[n_c+1],
+ * c_col int32[cap], c_ew int32[cap], c_vw int64[n_c] with cap >= the number
+ * of coarse entries (nnz is always enough); *c_nnz (host) receives the
+ * number of entries.  Coarse edge (x,y) has weight w(C_x, C_y) and exists
+ * iff it is positive; no self-loops; c_vw[x] = w(C_x); rows are unsorted. */
+LC_API int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                const int32_t *labels, int64_t n_c, const lc_opts *opts, int64_t *c_row_ptr,
+                int32_t *c_col, int32_t *c_ew, int64_t *c_vw, int64_t cap, int64_t *c_nnz);
+
+/* Exact objective of a clustering (Eq. 1): res->phi, res->objective,
+ * res->modularity and res->n_clusters (number of distinct labels).  labels:
+ * device int32[n] with values in [0, n). */
+LC_API int lc_objective(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                 int64_t lambda_num, int64_t lambda_den, const int32_t *labels,
+                 const lc_opts *opts, lc_result *res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LC_H */

@@ -49,7 +49,7 @@ typedef struct {
   const int64_t *row_ptr; /* n+1 */
   const int32_t *col;     /* nnz */
   const int32_t *ew;      /* nnz, w(u,v) > 0 */
-  const int64_t *vw;      /* n,   w(v) > 0 */
+  const int64_t *vw;      /* n,   w(v) >= 0 */
 } orc_graph;
 
 typedef struct {

@@ -1,0 +1,311 @@
+"""Python binding of liblc — GB300 (sm_103a) pLouvain / Louvain+ on LambdaCC.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``liblc.so`` behind the C ABI declared in ``include/lc.h``.  PyTorch
+provides device memory and the current CUDA stream.  If the native library
+is missing or cannot be loaded, every call raises; there is no CPU path.
+
+Functions carry the C names:
+  lc_cluster        Louvain+ (Algorithm 1) on device tensors
+  lc_cluster_host   the same on host (numpy) buffers, copies included
+  lc_local_move     one LocalMovePasses call (Algorithm 2 + Algorithm 3)
+  lc_contract       graph contraction (Algorithm 4)
+  lc_objective      exact LambdaCC objective (Eq. 1)
+  lc_strerror       name of an error code
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+LC_K_NAMES = ["first_pass", "move", "afterburner", "apply", "objective", "contract", "other"]
+
+
+class LCError(RuntimeError):
+    def __init__(self, code: int, detail: int = 0):
+        self.code = code
+        self.detail = detail
+        super().__init__(f"liblc error {code}: {lc_strerror(code)} (detail {detail})")
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class _Event(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("phase", ctypes.c_int32),
+                ("pass_", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("labels", ctypes.POINTER(ctypes.c_int32)), ("dest", ctypes.POINTER(ctypes.c_int32)),
+                ("moved", ctypes.POINTER(ctypes.c_uint8)),
+                ("phi", ctypes.c_int64), ("count_L", ctypes.c_int64), ("count_M", ctypes.c_int64),
+                ("cn", ctypes.c_int64), ("cnnz", ctypes.c_int64),
+                ("c_row_ptr", ctypes.POINTER(ctypes.c_int64)), ("c_col", ctypes.POINTER(ctypes.c_int32)),
+                ("c_ew", ctypes.POINTER(ctypes.c_int32)), ("c_vw", ctypes.POINTER(ctypes.c_int64))]
+
+
+_EventFn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(_Event))
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("pass_limit", ctypes.c_int32), ("phi_num", ctypes.c_int32 * 16),
+                ("phi_den", ctypes.c_int32 * 16), ("eps_num", ctypes.c_int32),
+                ("eps_den", ctypes.c_int32), ("seed", ctypes.c_uint32),
+                ("uncoarsen", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("passes_total", ctypes.c_int32), ("phi", ctypes.c_int64),
+                ("lambda_den", ctypes.c_int64), ("objective", ctypes.c_double),
+                ("modularity", ctypes.c_double), ("edges_local_move", ctypes.c_int64),
+                ("edges_contract", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 7),
+                ("kernel_launches", ctypes.c_int64 * 7), ("kernel_bytes", ctypes.c_double * 7),
+                ("error_detail", ctypes.c_int64)]
+
+
+EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_host", "lc_local_move",
+           "lc_contract", "lc_objective"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblc.so (building it in-tree if missing and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"liblc.so not built at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    csr, opts, res = ctypes.POINTER(_Csr), ctypes.POINTER(_Opts), ctypes.POINTER(_Result)
+    lib.lc_default_opts.argtypes = [opts]
+    lib.lc_default_opts.restype = None
+    lib.lc_strerror.argtypes = [ctypes.c_int]
+    lib.lc_strerror.restype = ctypes.c_char_p
+    lib.lc_cluster.argtypes = [csr, P, P, i64, i64, opts, P, res]
+    lib.lc_cluster_host.argtypes = [csr, P, P, i64, i64, opts, P, res]
+    lib.lc_local_move.argtypes = [csr, P, P, i64, i64, opts, P, i32, res]
+    lib.lc_contract.argtypes = [csr, P, P, P, i64, opts, P, P, P, P, i64, ctypes.POINTER(i64)]
+    lib.lc_objective.argtypes = [csr, P, P, i64, i64, P, opts, res]
+    for f in ("lc_cluster", "lc_cluster_host", "lc_local_move", "lc_contract", "lc_objective"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def lc_strerror(code: int) -> str:
+    return load().lc_strerror(code).decode()
+
+
+@dataclass
+class Options:
+    """Mirror of lc_opts (defaults of Section VI-C)."""
+
+    pass_limit: int = 6
+    phi: list = field(default_factory=lambda: [(3, 4)] * 4 + [(1, 4)] * 2)
+    eps: tuple = (1, 10)
+    seed: int = 0
+    uncoarsen: bool = True
+    validate: bool = True
+    profile: bool = False
+
+
+def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
+    o = o or Options()
+    c = _Opts()
+    load().lc_default_opts(ctypes.byref(c))
+    c.pass_limit = o.pass_limit
+    phi = list(o.phi) + [(1, 4)] * (16 - len(o.phi))
+    for i in range(16):
+        c.phi_num[i], c.phi_den[i] = phi[i]
+    c.eps_num, c.eps_den = o.eps
+    c.seed = o.seed & 0xFFFFFFFF
+    c.uncoarsen = int(bool(o.uncoarsen))
+    c.validate = int(bool(o.validate))
+    c.profile = int(bool(o.profile))
+    c.stream = stream
+    if event_fn is not None:
+        c.event_cb = event_fn
+    return c
+
+
+def _stream_handle(stream=None):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(0)
+
+
+def _result(r: _Result) -> dict:
+    out = {k: getattr(r, k) for k in ("n_clusters", "levels", "passes_total", "phi", "lambda_den",
+                                      "objective", "modularity", "edges_local_move", "edges_contract",
+                                      "error_detail")}
+    out["kernel_ms"] = dict(zip(LC_K_NAMES, list(r.kernel_ms)))
+    out["kernel_launches"] = dict(zip(LC_K_NAMES, list(r.kernel_launches)))
+    out["kernel_bytes"] = dict(zip(LC_K_NAMES, list(r.kernel_bytes)))
+    return out
+
+
+def _arr(ptr, n, dtype):
+    if n == 0 or not ptr:
+        return np.zeros(0, dtype=dtype)
+    return np.ctypeslib.as_array(ptr, shape=(n,)).copy()
+
+
+class Trace:
+    """Collects lc_event records (host copies) for parity checks."""
+
+    def __init__(self):
+        self.events = []
+        self.fn = _EventFn(self._on)
+
+    def _on(self, _ctx, evp):
+        ev = evp.contents
+        kind = {1: "pass", 2: "lmp", 3: "contract"}[ev.kind]
+        rec = {"kind": kind, "level": ev.level, "phase": "coarsen" if ev.phase == 0 else "uncoarsen",
+               "pass": ev.pass_, "n": ev.n, "C": _arr(ev.labels, ev.n, np.int32), "phi": ev.phi}
+        if kind == "pass":
+            rec.update(D=_arr(ev.dest, ev.n, np.int32), in_M=_arr(ev.moved, ev.n, np.uint8).astype(bool),
+                       count_L=ev.count_L, count_M=ev.count_M)
+        if kind == "contract":
+            rec.update(cn=ev.cn, cnnz=ev.cnnz, row_ptr=_arr(ev.c_row_ptr, ev.cn + 1, np.int64),
+                       col=_arr(ev.c_col, ev.cnnz, np.int32), ew=_arr(ev.c_ew, ev.cnnz, np.int32),
+                       vw=_arr(ev.c_vw, ev.cn, np.int64))
+        self.events.append(rec)
+
+
+def _check(rc: int, res: _Result | None = None):
+    if rc != 0:
+        raise LCError(rc, res.error_detail if res is not None else 0)
+
+
+def lc_cluster(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, opts: Options | None = None,
+               labels_out=None, stream=None, trace: Trace | None = None):
+    """Louvain+ on device tensors (row_ptr int64, col int32, ew int32, vw int64).
+    Returns (labels int32 CUDA tensor, result dict)."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    if labels_out is None:
+        labels_out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+    c = _c_opts(opts, _stream_handle(stream), trace.fn if trace else None)
+    res = _Result()
+    rc = lib.lc_cluster(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
+                        int(lambda_num), int(lambda_den), ctypes.byref(c),
+                        _dev(labels_out, torch.int32, "labels_out"), ctypes.byref(res))
+    _check(rc, res)
+    return labels_out, _result(res)
+
+
+def lc_cluster_host(row_ptr: np.ndarray, col: np.ndarray, ew: np.ndarray, vw: np.ndarray,
+                    lambda_num: int, lambda_den: int, opts: Options | None = None,
+                    labels_out: np.ndarray | None = None, stream=None):
+    """Louvain+ on host arrays; the C call copies in and out itself."""
+    lib = load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(ew, dtype=np.int32)
+    v = np.ascontiguousarray(vw, dtype=np.int64)
+    n = rp.shape[0] - 1
+    if labels_out is None:
+        labels_out = np.empty(max(n, 1), dtype=np.int32)
+    csr = _Csr(n, cl.shape[0], rp.ctypes.data, cl.ctypes.data if cl.size else None)
+    c = _c_opts(opts, _stream_handle(stream))
+    res = _Result()
+    rc = lib.lc_cluster_host(ctypes.byref(csr), v.ctypes.data if v.size else None,
+                             w.ctypes.data if w.size else None, int(lambda_num), int(lambda_den),
+                             ctypes.byref(c), labels_out.ctypes.data, ctypes.byref(res))
+    _check(rc, res)
+    return labels_out[:n], _result(res)
+
+
+def lc_local_move(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, labels,
+                  singleton_start: bool = False, opts: Options | None = None, stream=None,
+                  trace: Trace | None = None):
+    """One LocalMovePasses call; `labels` (int32 CUDA tensor) is replaced by C_out."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    c = _c_opts(opts, _stream_handle(stream), trace.fn if trace else None)
+    res = _Result()
+    rc = lib.lc_local_move(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
+                           int(lambda_num), int(lambda_den), ctypes.byref(c),
+                           _dev(labels, torch.int32, "labels"), int(bool(singleton_start)),
+                           ctypes.byref(res))
+    _check(rc, res)
+    return labels, _result(res)
+
+
+def lc_contract(row_ptr, col, ew, vw, labels, n_c: int, opts: Options | None = None, stream=None):
+    """Coarse graph of a dense clustering: (row_ptr, col, ew, vw) CUDA tensors."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    dev = row_ptr.device
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    cap = max(col.numel(), 1)
+    c_rp = torch.empty(n_c + 1, dtype=torch.int64, device=dev)
+    c_col = torch.empty(cap, dtype=torch.int32, device=dev)
+    c_ew = torch.empty(cap, dtype=torch.int32, device=dev)
+    c_vw = torch.empty(max(n_c, 1), dtype=torch.int64, device=dev)
+    out_nnz = ctypes.c_int64(0)
+    c = _c_opts(opts, _stream_handle(stream))
+    rc = lib.lc_contract(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
+                         _dev(labels, torch.int32, "labels"), int(n_c), ctypes.byref(c),
+                         _dev(c_rp, torch.int64, "c_row_ptr"), _dev(c_col, torch.int32, "c_col"),
+                         _dev(c_ew, torch.int32, "c_ew"), _dev(c_vw, torch.int64, "c_vw"), cap,
+                         ctypes.byref(out_nnz))
+    _check(rc)
+    m = out_nnz.value
+    return c_rp, c_col[:m], c_ew[:m], c_vw[:n_c]
+
+
+def lc_objective(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, labels,
+                 opts: Options | None = None, stream=None) -> dict:
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    c = _c_opts(opts, _stream_handle(stream))
+    res = _Result()
+    rc = lib.lc_objective(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
+                          int(lambda_num), int(lambda_den), _dev(labels, torch.int32, "labels"),
+                          ctypes.byref(c), ctypes.byref(res))
+    _check(rc, res)
+    return _result(res)

@@ -1,0 +1,852 @@
+// lc_api.cu — host driver of Louvain+ (Algorithm 1) and the C ABI of liblc.
+//
+// The driver issues every kernel on the caller's stream.  Per local-move
+// pass nothing is read back: the best-of test (Algorithm 2) and the
+// new-singleton bookkeeping run on the device.  Per level the host reads the
+// bin sizes, the cluster count n_c and the coarse edge count, which size the
+// launches and the coarse graph G_{l+1}.  All scratch memory comes from the
+// stream-ordered allocator and is sized once for G_0 and reused by every
+// coarser level (Section IV-C-1, memory reuse); only coarse graphs are
+// allocated per level.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lc_contract.cuh"
+#include "lc_internal.cuh"
+#include "lc_pass.cuh"
+#include "lc_scan.cuh"
+#include "lc_validate.cuh"
+
+namespace lc {
+
+// ------------------------------------------------------------ errors
+
+#define LC_CK(call)                                       \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      fprintf(stderr, "liblc: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
+              __FILE__, __LINE__);                        \
+      return e_ == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA; \
+    }                                                     \
+  } while (0)
+
+#define LC_TRY(expr)        \
+  do {                      \
+    int rc_ = (expr);       \
+    if (rc_ != LC_OK) return rc_; \
+  } while (0)
+
+static int launch_check() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "liblc: kernel launch failed: %s\n", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
+  }
+  return LC_OK;
+}
+
+// ------------------------------------------------------------- memory
+
+// Stream-ordered device allocations released together at scope exit.
+struct Arena {
+  cudaStream_t s;
+  std::vector<void *> ptrs;
+  explicit Arena(cudaStream_t st) : s(st) {}
+  Arena(const Arena &) = delete;
+  ~Arena() {
+    for (void *p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <class T>
+  int get(T **out, int64_t count) {
+    void *p = nullptr;
+    const size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *out = nullptr;
+      return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
+    }
+    ptrs.push_back(p);
+    *out = (T *)p;
+    return LC_OK;
+  }
+  void release(void *p) {
+    for (auto &q : ptrs)
+      if (q == p) {
+        cudaFreeAsync(p, s);
+        q = nullptr;
+      }
+  }
+};
+
+static void keep_pool_memory() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  configure_kernels();
+  cudaGetLastError();
+}
+
+// ------------------------------------------------------------ profile
+
+struct Prof {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  struct Span {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Span> spans;
+  int cur = -1;
+  cudaEvent_t cur_a = nullptr;
+  void begin(int cls) {
+    if (!on) return;
+    cur = cls;
+    cudaEventCreate(&cur_a);
+    cudaEventRecord(cur_a, s);
+  }
+  void end(double bytes) {
+    if (!on) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, s);
+    spans.push_back({cur, cur_a, b, bytes});
+  }
+  void finish(lc_result *res) {
+    for (auto &sp : spans) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+        res->kernel_ms[sp.cls] += ms;
+        res->kernel_bytes[sp.cls] += sp.bytes;
+      }
+      cudaEventDestroy(sp.a);
+      cudaEventDestroy(sp.b);
+    }
+    spans.clear();
+  }
+  ~Prof() {
+    for (auto &sp : spans) {
+      cudaEventDestroy(sp.a);
+      cudaEventDestroy(sp.b);
+    }
+  }
+};
+
+// ------------------------------------------------------------ the run
+
+struct Level {
+  LevelGraph g{};
+  Bins bins{};
+  int32_t *Cd = nullptr;  // dense coarsening clustering of this level
+  int64_t n_c = 0;
+};
+
+struct Run {
+  cudaStream_t s;
+  lc_opts o;
+  Method m;
+  lc_result *res;
+  Arena ar;
+  Prof prof;
+  // scratch sized for G_0
+  int32_t *C = nullptr, *D = nullptr, *C_out = nullptr, *freelist = nullptr, *used = nullptr,
+          *newid = nullptr, *cnt = nullptr, *scan32 = nullptr;
+  int64_t *W = nullptr, *delta = nullptr, *q = nullptr, *bound = nullptr, *off = nullptr,
+          *scan64 = nullptr;
+  uint8_t *M = nullptr, *E = nullptr;
+  unsigned long long *gtab = nullptr;
+  Scalars *sc = nullptr, *sc_trace = nullptr;
+  GraphStats *st = nullptr;
+  explicit Run(cudaStream_t st_) : s(st_), ar(st_) {}
+};
+
+static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
+  LC_TRY(r.ar.get(&r.C, n0));
+  LC_TRY(r.ar.get(&r.D, n0));
+  LC_TRY(r.ar.get(&r.C_out, n0));
+  LC_TRY(r.ar.get(&r.freelist, n0));
+  LC_TRY(r.ar.get(&r.used, n0));
+  LC_TRY(r.ar.get(&r.newid, n0));
+  LC_TRY(r.ar.get(&r.cnt, n0));
+  const int64_t big = 2 * nnz0 > n0 + 1 ? 2 * nnz0 : n0 + 1;
+  LC_TRY(r.ar.get(&r.scan32, scan_scratch(big)));
+  LC_TRY(r.ar.get(&r.W, n0));
+  LC_TRY(r.ar.get(&r.delta, n0));
+  LC_TRY(r.ar.get(&r.q, n0));
+  LC_TRY(r.ar.get(&r.bound, n0 + 1));
+  LC_TRY(r.ar.get(&r.off, n0 + 1));
+  LC_TRY(r.ar.get(&r.scan64, scan_scratch(n0 + 1)));
+  LC_TRY(r.ar.get(&r.M, n0));
+  LC_TRY(r.ar.get(&r.E, n0));
+  LC_TRY(r.ar.get(&r.gtab, 2 * nnz0));
+  LC_TRY(r.ar.get(&r.sc, 1));
+  LC_TRY(r.ar.get(&r.sc_trace, 1));
+  LC_CK(cudaMemsetAsync(r.gtab, 0, sizeof(unsigned long long) * (size_t)(2 * nnz0 > 0 ? 2 * nnz0 : 1), r.s));
+  LC_CK(cudaMemsetAsync(r.sc, 0, sizeof(Scalars), r.s));
+  return LC_OK;
+}
+
+static int bins_for(Run &r, Level &L) {
+  LC_TRY(r.ar.get(&L.bins.lists, L.g.n));
+  LC_TRY(r.ar.get(&L.bins.offs, kBins + 1));
+  build_bins(L.g, L.bins, r.scan32, r.s);
+  int32_t h[kBins + 1];
+  LC_CK(cudaMemcpyAsync(h, L.bins.offs, sizeof(h), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  finish_bins(L.bins, h);
+  r.res->kernel_launches[LC_K_OTHER] += 3 * kBins + kBins;
+  return launch_check();
+}
+
+static PassArgs pass_args(Run &r, const LevelGraph &g) {
+  PassArgs a{};
+  a.g = g;
+  a.m = r.m;
+  a.C = r.C;
+  a.W = r.W;
+  a.D = r.D;
+  a.delta = r.delta;
+  a.q = r.q;
+  a.M = r.M;
+  a.sc = r.sc;
+  a.gtab = r.gtab;
+  a.decide = 1;
+  return a;
+}
+
+static int nonempty_bins(const Bins &b) {
+  int k = 0;
+  for (int i = 0; i < kBins; ++i) k += b.count[i] > 0;
+  return k;
+}
+
+// Host copies for the optional trace callback.
+static int emit_pass_event(Run &r, const Level &L, int level, int phase, int pass) {
+  const int64_t n = L.g.n;
+  PassArgs a = pass_args(r, L.g);
+  a.sc = r.sc_trace;
+  LC_CK(cudaMemsetAsync(r.sc_trace, 0, sizeof(Scalars), r.s));
+  launch_objective(a, L.bins, r.s);
+  LC_TRY(launch_check());
+  std::vector<int32_t> C(n > 0 ? n : 1), D(n > 0 ? n : 1);
+  std::vector<uint8_t> M(n > 0 ? n : 1);
+  Scalars sct, sc;
+  LC_CK(cudaMemcpyAsync(C.data(), r.C, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(D.data(), r.D, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(M.data(), r.M, n, cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(&sct, r.sc_trace, sizeof(Scalars), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(&sc, r.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  // D of non-survivors is kept (candidates); M marks the afterburner survivors
+  lc_event ev;
+  memset(&ev, 0, sizeof(ev));
+  ev.kind = LC_EV_PASS;
+  ev.level = level;
+  ev.phase = phase;
+  ev.pass = pass;
+  ev.n = n;
+  ev.labels = C.data();
+  ev.dest = D.data();
+  ev.moved = M.data();
+  ev.phi = sct.phi_acc;
+  ev.count_L = sc.count_L;
+  ev.count_M = sc.count_M;
+  r.o.event_cb(r.o.event_ctx, &ev);
+  return LC_OK;
+}
+
+// Algorithm 2: `pass_limit` synchronous passes from r.C; leaves C_out (the
+// best clustering seen, strict improvement) in r.C_out and Phi(C_out) in
+// r.sc->phi_out.
+static int local_move_passes(Run &r, Level &L, bool singleton, int level, int phase) {
+  const int64_t n = L.g.n, nnz = L.g.nnz;
+  PassArgs a = pass_args(r, L.g);
+  const double nb = (double)nonempty_bins(L.bins);
+  if (singleton) {
+    launch_iota(r.C, n, r.s);
+    launch_iota(r.C_out, n, r.s);
+    LC_CK(cudaMemcpyAsync(r.W, L.g.vw, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, r.s));
+    r.res->kernel_launches[LC_K_OTHER] += 2;
+  } else {
+    launch_cluster_weights(r.C, L.g.vw, r.W, n, r.s);
+    r.res->kernel_launches[LC_K_OTHER] += 1;
+  }
+  Scalars init{};
+  init.phi_out = singleton ? 0 : LLONG_MIN;  // Phi(singletons) = 0
+  LC_CK(cudaMemcpyAsync(&r.sc->phi_acc, &init.phi_acc, sizeof(long long), cudaMemcpyHostToDevice, r.s));
+  LC_CK(cudaMemcpyAsync(&r.sc->phi_out, &init.phi_out, sizeof(long long), cudaMemcpyHostToDevice, r.s));
+  for (int i = 1; i <= r.o.pass_limit; ++i) {
+    a.phi_n = r.o.phi_num[i - 1];
+    a.phi_d = r.o.phi_den[i - 1];
+    launch_pass_begin(r.sc, r.s);
+    if (i == 1 && singleton) {
+      r.prof.begin(LC_K_FIRST_PASS);
+      launch_first_pass(a, L.bins, r.s);
+      r.prof.end(16.0 * nnz + 44.0 * n);
+      r.res->kernel_launches[LC_K_FIRST_PASS] += (int64_t)nb;
+    } else {
+      r.prof.begin(LC_K_MOVE);
+      launch_move(a, L.bins, r.s);
+      r.prof.end(12.0 * nnz + 48.0 * n);
+      r.res->kernel_launches[LC_K_MOVE] += (int64_t)nb;
+      r.prof.begin(LC_K_APPLY);
+      launch_bestof(r.sc, r.C, r.C_out, n, r.s);
+      r.prof.end(8.0 * n);
+      r.res->kernel_launches[LC_K_APPLY] += 2;
+    }
+    r.prof.begin(LC_K_AFTERBURNER);
+    launch_afterburner(a, L.bins, r.s);
+    r.prof.end(5.0 * n);
+    r.res->kernel_launches[LC_K_AFTERBURNER] += (int64_t)nb;
+    r.prof.begin(LC_K_APPLY);
+    launch_apply(a, r.E, r.used, r.freelist, r.scan32, r.s);
+    r.prof.end(14.0 * n);
+    r.res->kernel_launches[LC_K_APPLY] += 9;
+    LC_TRY(launch_check());
+    r.res->passes_total++;
+    r.res->edges_local_move += nnz;
+    if (r.o.event_cb) LC_TRY(emit_pass_event(r, L, level, phase, i));
+  }
+  r.prof.begin(LC_K_OBJECTIVE);
+  launch_objective(a, L.bins, r.s);
+  launch_bestof(r.sc, r.C, r.C_out, n, r.s);
+  r.prof.end(12.0 * nnz + 32.0 * n);
+  r.res->kernel_launches[LC_K_OBJECTIVE] += (int64_t)nb + 2;
+  LC_TRY(launch_check());
+  if (r.o.event_cb) {
+    std::vector<int32_t> C(n > 0 ? n : 1);
+    long long phi_out = 0;
+    LC_CK(cudaMemcpyAsync(C.data(), r.C_out, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(&phi_out, &r.sc->phi_out, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaStreamSynchronize(r.s));
+    lc_event ev;
+    memset(&ev, 0, sizeof(ev));
+    ev.kind = LC_EV_LMP;
+    ev.level = level;
+    ev.phase = phase;
+    ev.n = n;
+    ev.labels = C.data();
+    ev.phi = phi_out;
+    r.o.event_cb(r.o.event_ctx, &ev);
+  }
+  return LC_OK;
+}
+
+// Compacts r.C_out into L.Cd; returns n_c through *n_c (host).
+static int compact_level(Run &r, Level &L, int64_t *n_c) {
+  const int64_t n = L.g.n;
+  LC_TRY(r.ar.get(&L.Cd, n));
+  r.prof.begin(LC_K_CONTRACT);
+  launch_compact_labels(r.C_out, n, r.used, r.newid, L.Cd, r.scan32, r.s);
+  r.prof.end(24.0 * n);
+  r.res->kernel_launches[LC_K_CONTRACT] += 5;
+  int32_t k = 0;
+  LC_CK(cudaMemcpyAsync(&k, compact_total(r.scan32, n), sizeof(int32_t), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  LC_TRY(launch_check());
+  *n_c = k;
+  L.n_c = k;
+  return LC_OK;
+}
+
+// Algorithm 4 on (L.g, L.Cd) into a new level.
+static int contract_level(Run &r, Level &L, Level &N, int level) {
+  const int64_t n_c = L.n_c;
+  int64_t *rp_c = nullptr, *vw_c = nullptr;
+  LC_TRY(r.ar.get(&rp_c, n_c + 1));
+  LC_TRY(r.ar.get(&vw_c, n_c));
+  r.prof.begin(LC_K_CONTRACT);
+  launch_contract_offsets(L.g, L.Cd, n_c, r.bound, r.off, vw_c, r.scan64, r.s);
+  launch_contract_insert(L.g, L.Cd, r.off, r.gtab, r.cnt, n_c, &r.sc->error, L.bins.list,
+                         L.bins.count, r.s);
+  launch_contract_rowptr(r.cnt, n_c, rp_c, r.scan64, r.s);
+  r.prof.end(16.0 * L.g.nnz + 48.0 * L.g.n);
+  int64_t nnz_c = 0;
+  LC_CK(cudaMemcpyAsync(&nnz_c, rp_c + n_c, sizeof(int64_t), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  LC_TRY(launch_check());
+  int32_t *col_c = nullptr, *ew_c = nullptr;
+  LC_TRY(r.ar.get(&col_c, nnz_c));
+  LC_TRY(r.ar.get(&ew_c, nnz_c));
+  r.prof.begin(LC_K_CONTRACT);
+  launch_contract_compact(r.gtab, 2 * L.g.nnz, col_c, ew_c, r.scan32, r.s);
+  r.prof.end(16.0 * L.g.nnz + 8.0 * nnz_c);
+  r.res->kernel_launches[LC_K_CONTRACT] += 12 + nonempty_bins(L.bins);
+  LC_TRY(launch_check());
+  r.res->edges_contract += L.g.nnz;
+  N.g.n = n_c;
+  N.g.nnz = nnz_c;
+  N.g.rp = rp_c;
+  N.g.col = col_c;
+  N.g.ew = ew_c;
+  N.g.vw = vw_c;
+  if (r.o.event_cb) {
+    std::vector<int64_t> h_rp(n_c + 1), h_vw(n_c > 0 ? n_c : 1);
+    std::vector<int32_t> h_col(nnz_c > 0 ? nnz_c : 1), h_ew(nnz_c > 0 ? nnz_c : 1),
+        h_C(L.g.n > 0 ? L.g.n : 1);
+    LC_CK(cudaMemcpyAsync(h_rp.data(), rp_c, 8 * (n_c + 1), cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(h_vw.data(), vw_c, 8 * n_c, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(h_col.data(), col_c, 4 * nnz_c, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(h_ew.data(), ew_c, 4 * nnz_c, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(h_C.data(), L.Cd, 4 * L.g.n, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaStreamSynchronize(r.s));
+    lc_event ev;
+    memset(&ev, 0, sizeof(ev));
+    ev.kind = LC_EV_CONTRACT;
+    ev.level = level;
+    ev.n = L.g.n;
+    ev.labels = h_C.data();
+    ev.cn = n_c;
+    ev.cnnz = nnz_c;
+    ev.c_row_ptr = h_rp.data();
+    ev.c_col = h_col.data();
+    ev.c_ew = h_ew.data();
+    ev.c_vw = h_vw.data();
+    r.o.event_cb(r.o.event_ctx, &ev);
+  }
+  return LC_OK;
+}
+
+// ---------------------------------------------------------- arguments
+
+static int check_opts(const lc_opts &o) {
+  if (o.pass_limit < 0 || o.pass_limit > 16) return LC_ERR_ARG;
+  for (int i = 0; i < o.pass_limit; ++i)
+    if (o.phi_den[i] <= 0 || o.phi_num[i] < 0 || o.phi_num[i] > o.phi_den[i]) return LC_ERR_ARG;
+  if (o.eps_num <= 0 || o.eps_den <= 0) return LC_ERR_ARG;
+  return LC_OK;
+}
+
+static int check_graph_args(const lc_csr *g, const int64_t *vw, const int32_t *ew, int64_t mu,
+                            int64_t Lam) {
+  if (!g || g->n < 0 || g->n > INT32_MAX || g->nnz < 0) return LC_ERR_ARG;
+  if (g->n > 0 && (!g->row_ptr || !vw)) return LC_ERR_ARG;
+  if (g->nnz > 0 && (!g->col || !ew)) return LC_ERR_ARG;
+  if (Lam <= 0 || mu < 0 || mu > Lam) return LC_ERR_ARG;
+  return LC_OK;
+}
+
+// Statistics, validation and the exactness guards of the header.
+static int prepare(Run &r, const LevelGraph &g, GraphStats *hst) {
+  LC_TRY(r.ar.get(&r.st, 1));
+  GraphStats z{};
+  z.err_key = ~0ull;
+  LC_CK(cudaMemcpyAsync(r.st, &z, sizeof(z), cudaMemcpyHostToDevice, r.s));
+  int64_t ends[2] = {0, 0};
+  LC_CK(cudaMemcpyAsync(&ends[0], g.rp, 8, cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(&ends[1], g.rp + g.n, 8, cudaMemcpyDeviceToHost, r.s));
+  r.prof.begin(LC_K_OTHER);
+  launch_stats(g, r.o.validate, r.st, r.s);
+  r.prof.end(16.0 * g.n + 8.0 * g.nnz);
+  r.res->kernel_launches[LC_K_OTHER] += 1;
+  LC_CK(cudaMemcpyAsync(hst, r.st, sizeof(GraphStats), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  LC_TRY(launch_check());
+  if (ends[0] != 0 || ends[1] != g.nnz) return LC_ERR_ARG;
+  if (r.o.validate) {
+    if (hst->err_key != ~0ull) {
+      r.res->error_detail = (int64_t)(hst->err_key & 0xFFFFFFFFFFull);
+      return (int)(hst->err_key >> 40);
+    }
+    if (hst->fp1 != 0 || hst->fp2 != 0) return LC_ERR_ASYMMETRIC;
+  }
+  // exactness guards
+  const __int128 T = hst->T, V = hst->V;
+  if (T < 0 || T >= ((__int128)1 << 31)) return LC_ERR_OVERFLOW;
+  if (V < 0 || V >= ((__int128)1 << 62)) return LC_ERR_OVERFLOW;
+  const __int128 B = (__int128)r.m.Lam * T + (__int128)r.m.mu * V * V;
+  if (B >= ((__int128)1 << 60)) return LC_ERR_OVERFLOW;
+  const __int128 qb = (__int128)r.m.eps_den * 2 * B / ((__int128)r.m.eps_num * r.m.Lam);
+  if (qb >= ((__int128)1 << 60)) return LC_ERR_OVERFLOW;
+  return LC_OK;
+}
+
+static void fill_method(Run &r, int64_t mu, int64_t Lam) {
+  r.m.mu = mu;
+  r.m.Lam = Lam;
+  r.m.eps_num = r.o.eps_num;
+  r.m.eps_den = r.o.eps_den;
+  r.m.seed = r.o.seed;
+}
+
+static void finish_result(Run &r, lc_result *res, long long phi, const GraphStats &st) {
+  res->phi = phi;
+  res->lambda_den = r.m.Lam;
+  res->objective = (double)phi / (double)r.m.Lam;
+  const long long num = phi - (r.m.mu ? r.m.mu * st.sw2 : 0);
+  res->modularity = st.T > 0 ? (double)num / ((double)r.m.Lam * (double)st.T) : 0.0;
+}
+
+// Phi(labels) through the objective kernels (labels written to r.C first).
+static int objective_of(Run &r, Level &L, const int32_t *labels, long long *phi) {
+  const int64_t n = L.g.n;
+  LC_CK(cudaMemcpyAsync(r.C, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
+  launch_cluster_weights(r.C, L.g.vw, r.W, n, r.s);
+  PassArgs a = pass_args(r, L.g);
+  LC_CK(cudaMemsetAsync(r.sc, 0, sizeof(Scalars), r.s));
+  r.prof.begin(LC_K_OBJECTIVE);
+  launch_objective(a, L.bins, r.s);
+  r.prof.end(12.0 * L.g.nnz + 32.0 * n);
+  r.res->kernel_launches[LC_K_OBJECTIVE] += nonempty_bins(L.bins) + 1;
+  LC_CK(cudaMemcpyAsync(phi, &r.sc->phi_acc, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  return launch_check();
+}
+
+static int check_device_error(Run &r) {
+  int err = 0;
+  LC_CK(cudaMemcpyAsync(&err, &r.sc->error, sizeof(int), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  return err ? LC_ERR_DEVICE : LC_OK;
+}
+
+// Algorithm 1.
+static int cluster_impl(Run &r, const LevelGraph &g0, int32_t *labels_out) {
+  lc_result *res = r.res;
+  GraphStats st{};
+  LC_TRY(prepare(r, g0, &st));
+  LC_TRY(alloc_scratch(r, g0.n, g0.nnz));
+  std::vector<Level> lv(1);
+  lv[0].g = g0;
+  int top = 0;
+  for (int l = 0;; ++l) {
+    if (l >= kMaxLevels) return LC_ERR_TIMEOUT;
+    LC_TRY(bins_for(r, lv[l]));
+    LC_TRY(local_move_passes(r, lv[l], true, l, 0));
+    int64_t n_c = 0;
+    LC_TRY(compact_level(r, lv[l], &n_c));
+    if (n_c == lv[l].g.n) {
+      top = l;
+      break;
+    }
+    lv.emplace_back();
+    LC_TRY(contract_level(r, lv[l], lv[l + 1], l));
+  }
+  res->levels = top + 1;
+  // uncoarsening; the top level's C_out is the identity
+  launch_iota(r.C_out, lv[top].g.n, r.s);
+  for (int l = top - 1; l >= 0; --l) {
+    launch_project(lv[l].Cd, r.C_out, r.C, lv[l].g.n, r.s);
+    res->kernel_launches[LC_K_OTHER] += 1;
+    if (r.o.uncoarsen) {
+      LC_TRY(local_move_passes(r, lv[l], false, l, 1));
+    } else {
+      LC_CK(cudaMemcpyAsync(r.C_out, r.C, sizeof(int32_t) * lv[l].g.n, cudaMemcpyDeviceToDevice, r.s));
+    }
+  }
+  // final dense labels and the exact objective
+  const int64_t n = g0.n;
+  launch_compact_labels(r.C_out, n, r.used, r.newid, labels_out, r.scan32, r.s);
+  res->kernel_launches[LC_K_CONTRACT] += 5;
+  int32_t k = 0;
+  LC_CK(cudaMemcpyAsync(&k, compact_total(r.scan32, n), sizeof(int32_t), cudaMemcpyDeviceToHost, r.s));
+  long long phi = 0;
+  LC_TRY(objective_of(r, lv[0], labels_out, &phi));
+  res->n_clusters = k;
+  LC_TRY(check_device_error(r));
+  finish_result(r, res, phi, st);
+  return LC_OK;
+}
+
+static lc_opts resolve_opts(const lc_opts *o) {
+  lc_opts d;
+  lc_default_opts(&d);
+  return o ? *o : d;
+}
+
+static int begin_call(Run &r, const lc_opts *opts, lc_result *res) {
+  r.o = resolve_opts(opts);
+  r.res = res;
+  memset(res, 0, sizeof(*res));
+  LC_TRY(check_opts(r.o));
+  keep_pool_memory();
+  r.prof.on = r.o.profile != 0;
+  r.prof.s = r.s;
+  return LC_OK;
+}
+
+static void end_call(Run &r, int rc) {
+  if (r.prof.on) {
+    cudaStreamSynchronize(r.s);
+    r.prof.finish(r.res);
+  }
+  if (rc != LC_OK) {
+    int64_t detail = r.res->error_detail;
+    memset(r.res, 0, sizeof(*r.res));
+    r.res->error_detail = detail;
+  }
+}
+
+}  // namespace lc
+
+// ================================================================ C ABI
+
+using namespace lc;
+
+extern "C" {
+
+void lc_default_opts(lc_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->pass_limit = 6;
+  for (int i = 0; i < 16; ++i) {
+    o->phi_num[i] = i < 4 ? 3 : 1;
+    o->phi_den[i] = 4;
+  }
+  o->eps_num = 1;
+  o->eps_den = 10;
+  o->seed = 0;
+  o->uncoarsen = 1;
+  o->validate = 1;
+  o->profile = 0;
+  o->stream = nullptr;
+  o->event_cb = nullptr;
+  o->event_ctx = nullptr;
+}
+
+const char *lc_strerror(int code) {
+  switch (code) {
+    case LC_OK: return "ok";
+    case LC_ERR_ARG: return "invalid argument";
+    case LC_ERR_ASYMMETRIC: return "graph is not symmetric";
+    case LC_ERR_SELF_LOOP: return "graph has a self-loop";
+    case LC_ERR_DUPLICATE: return "row not strictly increasing (duplicate or unsorted)";
+    case LC_ERR_WEIGHT: return "non-positive weight";
+    case LC_ERR_OVERFLOW: return "exactness guard exceeded";
+    case LC_ERR_OOM: return "device out of memory";
+    case LC_ERR_CUDA: return "CUDA error";
+    case LC_ERR_TIMEOUT: return "level limit reached";
+    case LC_ERR_DEVICE: return "kernel bound violation";
+    case LC_ERR_NOT_READY: return "not ready";
+    default: return "unknown error";
+  }
+}
+
+int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
+               int64_t lambda_den, const lc_opts *opts, int32_t *labels_out, lc_result *res) {
+  if (!res) return LC_ERR_ARG;
+  lc_opts o = resolve_opts(opts);
+  Run r((cudaStream_t)o.stream);
+  int rc = begin_call(r, opts, res);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  if (rc == LC_OK && g->n > 0 && !labels_out) rc = LC_ERR_ARG;
+  if (rc == LC_OK && g->n > 0) {
+    fill_method(r, lambda_num, lambda_den);
+    LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
+    rc = cluster_impl(r, g0, labels_out);
+  } else if (rc == LC_OK) {
+    res->lambda_den = lambda_den;
+  }
+  end_call(r, rc);
+  return rc;
+}
+
+int lc_cluster_host(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                    int64_t lambda_num, int64_t lambda_den, const lc_opts *opts,
+                    int32_t *labels_out, lc_result *res) {
+  if (!res) return LC_ERR_ARG;
+  int rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  if (rc != LC_OK) return rc;
+  if (g->n > 0 && !labels_out) return LC_ERR_ARG;
+  lc_opts o = resolve_opts(opts);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Arena ar(s);
+  int64_t *d_rp = nullptr, *d_vw = nullptr;
+  int32_t *d_col = nullptr, *d_ew = nullptr, *d_lab = nullptr;
+  const int64_t n = g->n, nnz = g->nnz;
+  if ((rc = ar.get(&d_rp, n + 1)) || (rc = ar.get(&d_vw, n)) || (rc = ar.get(&d_col, nnz)) ||
+      (rc = ar.get(&d_ew, nnz)) || (rc = ar.get(&d_lab, n)))
+    return rc;
+  if (n > 0) {
+    cudaMemcpyAsync(d_rp, g->row_ptr, 8 * (n + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_vw, vertex_w, 8 * n, cudaMemcpyHostToDevice, s);
+  }
+  if (nnz > 0) {
+    cudaMemcpyAsync(d_col, g->col, 4 * nnz, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_ew, edge_w, 4 * nnz, cudaMemcpyHostToDevice, s);
+  }
+  if (cudaGetLastError() != cudaSuccess) return LC_ERR_CUDA;
+  lc_csr dg{n, nnz, d_rp, d_col};
+  rc = lc_cluster(&dg, d_vw, d_ew, lambda_num, lambda_den, &o, d_lab, res);
+  if (rc == LC_OK && n > 0) {
+    if (cudaMemcpyAsync(labels_out, d_lab, 4 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = LC_ERR_CUDA;
+  }
+  return rc;
+}
+
+int lc_local_move(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                  int64_t lambda_num, int64_t lambda_den, const lc_opts *opts,
+                  int32_t *labels_inout, int32_t singleton_start, lc_result *res) {
+  if (!res) return LC_ERR_ARG;
+  lc_opts o = resolve_opts(opts);
+  Run r((cudaStream_t)o.stream);
+  int rc = begin_call(r, opts, res);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  if (rc == LC_OK && g->n > 0 && !labels_inout) rc = LC_ERR_ARG;
+  if (rc == LC_OK && g->n > 0) {
+    fill_method(r, lambda_num, lambda_den);
+    LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
+    GraphStats st{};
+    rc = prepare(r, g0, &st);
+    if (rc == LC_OK) {
+      launch_labels_in_range(labels_inout, g0.n, g0.n, r.st, r.s);
+      GraphStats st2{};
+      if (cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
+          cudaStreamSynchronize(r.s) != cudaSuccess)
+        rc = LC_ERR_CUDA;
+      else if (st2.err_key != ~0ull)
+        rc = LC_ERR_ARG;
+    }
+    if (rc == LC_OK) rc = alloc_scratch(r, g0.n, g0.nnz);
+    Level L;
+    L.g = g0;
+    if (rc == LC_OK) rc = bins_for(r, L);
+    if (rc == LC_OK) {
+      cudaMemcpyAsync(r.C, labels_inout, 4 * g0.n, cudaMemcpyDeviceToDevice, r.s);
+      rc = local_move_passes(r, L, singleton_start != 0, 0, singleton_start ? 0 : 1);
+    }
+    if (rc == LC_OK) {
+      cudaMemcpyAsync(labels_inout, r.C_out, 4 * g0.n, cudaMemcpyDeviceToDevice, r.s);
+      long long phi = 0;
+      if (cudaMemcpyAsync(&phi, &r.sc->phi_out, 8, cudaMemcpyDeviceToHost, r.s) != cudaSuccess)
+        rc = LC_ERR_CUDA;
+      int32_t k = 0;
+      if (rc == LC_OK) {
+        launch_compact_labels(labels_inout, g0.n, r.used, r.newid, nullptr, r.scan32, r.s);
+        if (cudaMemcpyAsync(&k, compact_total(r.scan32, g0.n), 4, cudaMemcpyDeviceToHost, r.s) !=
+            cudaSuccess)
+          rc = LC_ERR_CUDA;
+      }
+      if (rc == LC_OK) rc = check_device_error(r);
+      if (rc == LC_OK) {
+        res->n_clusters = k;
+        res->levels = 1;
+        finish_result(r, res, phi, st);
+      }
+    }
+  }
+  end_call(r, rc);
+  return rc;
+}
+
+int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                const int32_t *labels, int64_t n_c, const lc_opts *opts, int64_t *c_row_ptr,
+                int32_t *c_col, int32_t *c_ew, int64_t *c_vw, int64_t cap, int64_t *c_nnz) {
+  int rc = check_graph_args(g, vertex_w, edge_w, 0, 1);
+  if (rc != LC_OK) return rc;
+  if (n_c < 0 || n_c > g->n || !c_nnz || (g->n > 0 && (!labels || !c_row_ptr || !c_vw)) ||
+      cap < 0 || (cap > 0 && (!c_col || !c_ew)))
+    return LC_ERR_ARG;
+  if (g->n > 0 && n_c == 0) return LC_ERR_ARG;
+  lc_result tmp;
+  lc_opts o = resolve_opts(opts);
+  Run r((cudaStream_t)o.stream);
+  rc = begin_call(r, opts, &tmp);
+  if (rc != LC_OK) return rc;
+  *c_nnz = 0;
+  if (g->n == 0) {
+    if (c_row_ptr) cudaMemsetAsync(c_row_ptr, 0, 8, r.s);
+    return cudaStreamSynchronize(r.s) == cudaSuccess ? LC_OK : LC_ERR_CUDA;
+  }
+  fill_method(r, 0, 1);
+  LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
+  GraphStats st{};
+  rc = prepare(r, g0, &st);
+  if (rc == LC_OK) {
+    launch_labels_in_range(labels, g0.n, n_c, r.st, r.s);
+    GraphStats st2{};
+    if (cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
+        cudaStreamSynchronize(r.s) != cudaSuccess)
+      rc = LC_ERR_CUDA;
+    else if (st2.err_key != ~0ull)
+      rc = LC_ERR_ARG;
+  }
+  if (rc == LC_OK) rc = alloc_scratch(r, g0.n, g0.nnz);
+  Level L;
+  L.g = g0;
+  if (rc == LC_OK) rc = bins_for(r, L);
+  if (rc == LC_OK) {
+    L.Cd = const_cast<int32_t *>(labels);
+    L.n_c = n_c;
+    launch_contract_offsets(L.g, L.Cd, n_c, r.bound, r.off, c_vw, r.scan64, r.s);
+    launch_contract_insert(L.g, L.Cd, r.off, r.gtab, r.cnt, n_c, &r.sc->error, L.bins.list,
+                           L.bins.count, r.s);
+    launch_contract_rowptr(r.cnt, n_c, c_row_ptr, r.scan64, r.s);
+    int64_t nnz_c = 0;
+    if (cudaMemcpyAsync(&nnz_c, c_row_ptr + n_c, 8, cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
+        cudaStreamSynchronize(r.s) != cudaSuccess)
+      rc = LC_ERR_CUDA;
+    if (rc == LC_OK && nnz_c > cap) {
+      rc = LC_ERR_ARG;
+      r.res->error_detail = nnz_c;
+    }
+    if (rc == LC_OK) {
+      launch_contract_compact(r.gtab, 2 * g0.nnz, c_col, c_ew, r.scan32, r.s);
+      rc = launch_check();
+    }
+    if (rc == LC_OK) rc = check_device_error(r);
+    if (rc == LC_OK) *c_nnz = nnz_c;
+  }
+  end_call(r, rc);
+  return rc;
+}
+
+int lc_objective(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                 int64_t lambda_num, int64_t lambda_den, const int32_t *labels,
+                 const lc_opts *opts, lc_result *res) {
+  if (!res) return LC_ERR_ARG;
+  lc_opts o = resolve_opts(opts);
+  Run r((cudaStream_t)o.stream);
+  int rc = begin_call(r, opts, res);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  if (rc == LC_OK && g->n > 0 && !labels) rc = LC_ERR_ARG;
+  if (rc == LC_OK && g->n > 0) {
+    fill_method(r, lambda_num, lambda_den);
+    LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
+    GraphStats st{};
+    rc = prepare(r, g0, &st);
+    if (rc == LC_OK) {
+      launch_labels_in_range(labels, g0.n, g0.n, r.st, r.s);
+      GraphStats st2{};
+      if (cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
+          cudaStreamSynchronize(r.s) != cudaSuccess)
+        rc = LC_ERR_CUDA;
+      else if (st2.err_key != ~0ull)
+        rc = LC_ERR_ARG;
+    }
+    if (rc == LC_OK) rc = alloc_scratch(r, g0.n, 0);
+    Level L;
+    L.g = g0;
+    if (rc == LC_OK) rc = bins_for(r, L);
+    long long phi = 0;
+    if (rc == LC_OK) rc = objective_of(r, L, labels, &phi);
+    if (rc == LC_OK) {
+      launch_compact_labels(labels, g0.n, r.used, r.newid, nullptr, r.scan32, r.s);
+      int32_t k = 0;
+      if (cudaMemcpyAsync(&k, compact_total(r.scan32, g0.n), 4, cudaMemcpyDeviceToHost, r.s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(r.s) != cudaSuccess)
+        rc = LC_ERR_CUDA;
+      res->n_clusters = k;
+      res->levels = 1;
+      finish_result(r, res, phi, st);
+    }
+  }
+  end_call(r, rc);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// lc_contract.cu — label compaction, gather-free graph contraction
+// (Algorithm 4) and projection (Algorithm 1, ProjectCluster).
+//
+// Contraction works per FINE vertex (no gathering of fine vertices by
+// cluster): coarse vertex x owns the region [2 off[x], 2 off[x+1]) of the
+// global hash scratch, where off is the exclusive prefix sum of
+// bound[x] = sum of deg(v) over v in C_x (an upper bound on x's distinct
+// coarse neighbours, so the load factor stays <= 1/2).  Every fine edge
+// (v,u) with C[u] != C[v] is inserted into C[v]'s region; the insert that
+// claims a new slot also counts a unique coarse edge of x.  The coarse
+// offsets are a scan of those counts and the coarse CSR is one stream
+// compaction over all regions, which also resets the slots for reuse.
+#include <climits>
+
+#include "lc_contract.cuh"
+#include "lc_group.cuh"
+#include "lc_internal.cuh"
+#include "lc_scan.cuh"
+
+namespace lc {
+
+__global__ void k_mark_used(const int32_t *__restrict__ C, int32_t *__restrict__ used, int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    used[C[v]] = 1;
+}
+
+struct UsedIn {
+  const int32_t *used;
+  __device__ int32_t operator()(int64_t x) const { return used[x]; }
+};
+struct NewIdOut {
+  int32_t *newid;
+  __device__ void operator()(int64_t x, int32_t pos, int32_t) const { newid[x] = pos; }
+};
+
+__global__ void k_relabel(const int32_t *__restrict__ C, const int32_t *__restrict__ newid,
+                          int32_t *__restrict__ out, int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = newid[C[v]];
+}
+
+// bound[C[v]] += deg(v), vw_c[C[v]] += w(v)
+__global__ void k_bound(LevelGraph g, const int32_t *__restrict__ Cd, int64_t *bound, int64_t *vw_c) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = Cd[v];
+    const int64_t d = g.rp[v + 1] - g.rp[v];
+    if (d) atomicAdd((unsigned long long *)&bound[x], (unsigned long long)d);
+    atomicAdd((unsigned long long *)&vw_c[x], (unsigned long long)g.vw[v]);
+  }
+}
+
+struct I64In {
+  const int64_t *a;
+  __device__ int64_t operator()(int64_t i) const { return a[i]; }
+};
+struct I64Out {
+  int64_t *o;
+  __device__ void operator()(int64_t i, int64_t pos, int64_t) const { o[i] = pos; }
+};
+
+struct InsertArgs {
+  LevelGraph g;
+  const int32_t *Cd;
+  const int64_t *off;
+  unsigned long long *tab;
+  int32_t *cnt;
+  int *error;
+};
+
+// Insert every fine edge of v leaving C[v] into the coarse table of C[v].
+template <int GS>
+__global__ void __launch_bounds__(GS > 32 ? GS : 256)
+    k_insert(InsertArgs a, const int32_t *__restrict__ list, int64_t count) {
+  const int r = Grp<GS>::rank();
+  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
+    if (!active) return;
+    const int32_t v = list[i];
+    const int32_t x = a.Cd[v];
+    const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
+    const int64_t o0 = a.off[x];
+    const uint32_t cap = (uint32_t)(2 * (a.off[x + 1] - o0));
+    unsigned long long *tab = a.tab + 2 * o0;
+    int fresh_n = 0;
+    bool ok = true;
+    for (int64_t e = beg + r; e < end; e += GS) {
+      const int32_t y = a.Cd[__ldg(a.g.col + e)];
+      if (y == x) continue;
+      bool fresh = false;
+      ok &= table_add(tab, cap, y, __ldg(a.g.ew + e), fresh);
+      fresh_n += fresh;
+    }
+    if (!ok) *a.error = 1;
+    if (fresh_n) atomicAdd(&a.cnt[x], fresh_n);
+  });
+}
+
+struct CntIn {
+  const int32_t *cnt;
+  __device__ int64_t operator()(int64_t i) const { return cnt[i]; }
+};
+
+struct SlotIn {
+  const unsigned long long *tab;
+  __device__ int32_t operator()(int64_t s) const { return tab[s] != kEmptySlot ? 1 : 0; }
+};
+struct SlotOut {
+  unsigned long long *tab;
+  int32_t *col;
+  int32_t *ew;
+  __device__ void operator()(int64_t s, int32_t pos, int32_t f) const {
+    if (f) {
+      const unsigned long long t = tab[s];
+      col[pos] = slot_key(t);
+      ew[pos] = slot_val(t);
+      tab[s] = kEmptySlot;
+    }
+  }
+};
+
+__global__ void k_project(const int32_t *__restrict__ Cd, const int32_t *__restrict__ Cnext,
+                          int32_t *__restrict__ C, int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    C[v] = Cnext[Cd[v]];
+}
+
+// ================================================================= host
+
+static inline unsigned blocks_for(int64_t items, int per_block) {
+  int64_t b = (items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+void launch_compact_labels(const int32_t *C, int64_t n, int32_t *used, int32_t *newid,
+                           int32_t *Cd, int32_t *scan_tmp, cudaStream_t s) {
+  cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s);
+  k_mark_used<<<blocks_for(n, 256), 256, 0, s>>>(C, used, n);
+  scan_apply<int32_t>(n, UsedIn{used}, NewIdOut{newid}, scan_tmp, s);
+  if (Cd) k_relabel<<<blocks_for(n, 256), 256, 0, s>>>(C, newid, Cd, n);
+}
+
+const int32_t *compact_total(const int32_t *scan_tmp, int64_t n) {
+  return scan_tmp + scan_tiles(n);
+}
+
+void launch_contract_offsets(const LevelGraph &g, const int32_t *Cd, int64_t n_c, int64_t *bound,
+                             int64_t *off, int64_t *vw_c, int64_t *scan_tmp64, cudaStream_t s) {
+  cudaMemsetAsync(bound, 0, sizeof(int64_t) * (size_t)(n_c + 1), s);
+  cudaMemsetAsync(vw_c, 0, sizeof(int64_t) * (size_t)(n_c > 0 ? n_c : 1), s);
+  k_bound<<<blocks_for(g.n, 256), 256, 0, s>>>(g, Cd, bound, vw_c);
+  scan_apply<int64_t>(n_c + 1, I64In{bound}, I64Out{off}, scan_tmp64, s);
+}
+
+template <int GS>
+static void launch_insert(const InsertArgs &a, const int32_t *list, int64_t count, cudaStream_t s) {
+  if (count <= 0) return;
+  const int threads = GS > 32 ? GS : 256;
+  const int per_block = GS > 32 ? 1 : threads / GS;
+  k_insert<GS><<<blocks_for(count, per_block), threads, 0, s>>>(a, list, count);
+}
+
+void launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t *off,
+                            unsigned long long *tab, int32_t *cnt, int64_t n_c, int *error,
+                            const int32_t *const *lists, const int64_t *counts, cudaStream_t s) {
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n_c > 0 ? n_c : 1), s);
+  InsertArgs a{g, Cd, off, tab, cnt, error};
+  launch_insert<8>(a, lists[0], counts[0], s);
+  launch_insert<32>(a, lists[1], counts[1], s);
+  launch_insert<32>(a, lists[2], counts[2], s);
+  launch_insert<kBin3Threads>(a, lists[3], counts[3], s);
+  launch_insert<kBin4Threads>(a, lists[4], counts[4], s);
+}
+
+void launch_contract_rowptr(const int32_t *cnt, int64_t n_c, int64_t *rp_c, int64_t *scan_tmp64,
+                            cudaStream_t s) {
+  scan_apply<int64_t>(n_c, CntIn{cnt}, I64Out{rp_c}, scan_tmp64, s);
+  cudaMemcpyAsync(rp_c + n_c, scan_tmp64 + scan_tiles(n_c), sizeof(int64_t),
+                  cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_contract_compact(unsigned long long *tab, int64_t slots, int32_t *col_c, int32_t *ew_c,
+                             int32_t *scan_tmp, cudaStream_t s) {
+  scan_apply<int32_t>(slots, SlotIn{tab}, SlotOut{tab, col_c, ew_c}, scan_tmp, s);
+}
+
+void launch_project(const int32_t *Cd, const int32_t *Cnext, int32_t *C, int64_t n, cudaStream_t s) {
+  k_project<<<blocks_for(n, 256), 256, 0, s>>>(Cd, Cnext, C, n);
+}
+
+}  // namespace lc

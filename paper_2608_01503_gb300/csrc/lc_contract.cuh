@@ -1,0 +1,31 @@
+// lc_contract.cuh — launch interface of lc_contract.cu.
+#pragma once
+
+#include "lc_internal.cuh"
+
+namespace lc {
+
+// Dense relabelling of the ids in use (ascending old id -> 0..k-1):
+// used/newid are int32[n] scratch; Cd (nullable) receives newid[C[v]].
+// The count k is left in *compact_total(scan_tmp, n) on the device.
+void launch_compact_labels(const int32_t *C, int64_t n, int32_t *used, int32_t *newid,
+                           int32_t *Cd, int32_t *scan_tmp, cudaStream_t s);
+const int32_t *compact_total(const int32_t *scan_tmp, int64_t n);
+
+// Algorithm 4, lines 1-4: bound, offsets (int64[n_c+1]) and coarse vertex weights.
+void launch_contract_offsets(const LevelGraph &g, const int32_t *Cd, int64_t n_c, int64_t *bound,
+                             int64_t *off, int64_t *vw_c, int64_t *scan_tmp64, cudaStream_t s);
+// Algorithm 4, lines 5-12: inserts with unique counting (cnt int32[n_c]).
+void launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t *off,
+                            unsigned long long *tab, int32_t *cnt, int64_t n_c, int *error,
+                            const int32_t *const *lists, const int64_t *counts, cudaStream_t s);
+// Coarse row offsets from the unique counts; rp_c[n_c] = nnz_c.
+void launch_contract_rowptr(const int32_t *cnt, int64_t n_c, int64_t *rp_c, int64_t *scan_tmp64,
+                            cudaStream_t s);
+// Algorithm 4, line 13: stream compaction of all table slots into the coarse CSR.
+void launch_contract_compact(unsigned long long *tab, int64_t slots, int32_t *col_c, int32_t *ew_c,
+                             int32_t *scan_tmp, cudaStream_t s);
+// C[v] = Cnext[Cd[v]]
+void launch_project(const int32_t *Cd, const int32_t *Cnext, int32_t *C, int64_t n, cudaStream_t s);
+
+}  // namespace lc

@@ -1,0 +1,206 @@
+// lc_internal.cuh — internal types and device helpers of liblc (sm_103a).
+//
+// Notation follows Section II of the paper: lambda = mu / Lam, w(v) vertex
+// weights, w(u,v) edge weights, S(v,X) = sum of w(u,v) over neighbours u of v
+// in cluster X, W(X) = sum of w(u) over u in X.  Gains are Lam-scaled so they
+// are exact int64:  g(v,X) = Lam*S(v,X) - mu*w(v)*(W(X) - [X = C[v]] w(v)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lc.h"
+
+namespace lc {
+
+constexpr int32_t kNone = -1;   // D[v]: v is not a candidate
+constexpr int32_t kEmpty = -2;  // D[v]: move v to a new empty cluster
+// Hash slot = [key + 1 : 32 | value : 32]; 0 is an empty slot, so a table is
+// cleared with a plain memset.
+constexpr unsigned long long kEmptySlot = 0ull;
+constexpr int kMaxLevels = 256;
+
+// Degree bins of the per-vertex kernels.  A vertex of degree d is handled by
+//   bin 0: d <= 8       a group of 8 lanes (4 vertices per warp), one neighbour per lane
+//   bin 1: d <= 32      one warp, one neighbour per lane
+//   bin 2: d <= 256     one warp; aggregation in a shared-memory table of <= 512 slots
+//   bin 3: d <= 4096    one 256-thread block; shared-memory table of <= 8192 slots
+//   bin 4: d >  4096    one 512-thread block; global-memory table of 2d slots
+constexpr int kBins = 5;
+constexpr int64_t kBinMaxDeg[kBins - 1] = {8, 32, 256, 4096};
+constexpr int kBin2Warps = 8;        // warps per block in bin 2
+constexpr int kBin2Slots = 512;      // table slots per warp in bin 2
+constexpr int kBin3Threads = 256;
+constexpr int kBin3Slots = 8192;
+constexpr int kBin4Threads = 512;
+
+// One level's graph G_l (device pointers).
+struct LevelGraph {
+  int64_t n, nnz;
+  const int64_t *rp;
+  const int32_t *col;
+  const int32_t *ew;
+  const int64_t *vw;
+};
+
+// Method constants of one call.
+struct Method {
+  int64_t mu, Lam;        // lambda = mu / Lam
+  int32_t eps_num, eps_den;
+  uint32_t seed;
+};
+
+// Per-pass arrays (device), all of length n of the current level.
+struct PassState {
+  int32_t *C;       // current clustering, values in [0, n)
+  int64_t *W;       // W(X) per label X in [0, n)
+  int32_t *D;       // destination for candidates, kNone otherwise
+  int64_t *delta;   // g(v,D[v]) - g(v,C[v]) for candidates
+  int64_t *q;       // epsilon bucket of delta for candidates
+  uint8_t *M;       // afterburner survivors
+  int32_t *C_out;   // best clustering seen
+  // scalars (device), see Scalars below
+};
+
+// Device-resident scalars of one LocalMovePasses call.
+struct Scalars {
+  long long phi_acc;     // Phi of the clustering entering the current pass
+  long long phi_out;     // Phi(C_out)
+  int improved;          // phi_acc > phi_out at the last best-of test
+  int empty_movers;      // movers to a new empty cluster in this pass
+  long long count_L, count_M;
+  int error;             // internal bound violation (hash probe overrun)
+  int pad;
+};
+
+// ------------------------------------------------------------------ hashes
+
+// MurmurHash3 32-bit finaliser (Appleby), a published bijective mixer.
+__host__ __device__ inline uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Slot of a cluster id in a table of `cap` slots (multiplicative hash then
+// Lemire's multiply-shift range reduction; cap need not be a power of two).
+__device__ __forceinline__ uint32_t slot_of(int32_t key, uint32_t cap) {
+  uint32_t h = (uint32_t)key * 0x9E3779B1u;
+  return (uint32_t)(((uint64_t)h * cap) >> 32);
+}
+
+__device__ __forceinline__ int32_t slot_key(unsigned long long s) {
+  return (int32_t)((uint32_t)(s >> 32) - 1u);
+}
+__device__ __forceinline__ int32_t slot_val(unsigned long long s) { return (int32_t)(uint32_t)s; }
+
+// Insert (key, w) into an open-addressing table of `cap` 64-bit slots with
+// linear probing.  A new key is claimed and its first weight stored in one
+// compare-and-swap; later weights of the key are one atomic add on the low
+// word (values stay below 2^31, so the add never carries into the key).
+// Returns false when all `cap` slots were probed without success, a bound
+// violation (every caller sizes tables to at least twice its distinct keys).
+// `fresh` is set when this call claimed a new slot.
+__device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap, int32_t key,
+                                          int32_t w, bool &fresh) {
+  const unsigned long long tag = (unsigned long long)((uint32_t)key + 1u) << 32;
+  uint32_t s = slot_of(key, cap);
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    unsigned long long cur = tab[s];
+    if (cur == kEmptySlot) {
+      unsigned long long prev = atomicCAS(&tab[s], kEmptySlot, tag | (uint32_t)w);
+      if (prev == kEmptySlot) {
+        fresh = true;
+        return true;
+      }
+      cur = prev;
+    }
+    if ((cur & 0xFFFFFFFF00000000ull) == tag) {
+      atomicAdd(&tab[s], (unsigned long long)(uint32_t)w);
+      return true;
+    }
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return false;
+}
+
+// --------------------------------------------------------------- gains
+
+// Lam-scaled gain of joining cluster X (X != C[v]): Lam*S - mu*w(v)*W(X).
+__device__ __forceinline__ long long gain_other(const Method &m, long long S, long long wv,
+                                                long long WX) {
+  return m.Lam * S - m.mu * wv * WX;
+}
+// Lam-scaled gain of staying: Lam*S_self - mu*w(v)*(W(C[v]) - w(v)).
+__device__ __forceinline__ long long gain_self(const Method &m, long long S, long long wv,
+                                               long long WC) {
+  return m.Lam * S - m.mu * wv * (WC - wv);
+}
+
+// Better (gain, id) for the argmax: larger gain, ties to the smaller id.
+__device__ __forceinline__ bool better(long long g1, int32_t x1, long long g2, int32_t x2) {
+  return g1 > g2 || (g1 == g2 && (uint32_t)x1 < (uint32_t)x2);
+}
+
+// floor(eps_den * delta / (eps_num * Lam)), the epsilon bucket of the
+// ordering of Section IV-A-1.
+__device__ __forceinline__ long long eps_bucket(const Method &m, long long delta) {
+  __int128 num = (__int128)m.eps_den * delta;
+  __int128 den = (__int128)m.eps_num * m.Lam;
+  __int128 qq = num / den;
+  if ((num % den) != 0 && num < 0) qq -= 1;
+  return (long long)qq;
+}
+
+// ord(u) < ord(v): larger bucket first, then smaller hash, then smaller id.
+__device__ __forceinline__ bool earlier(long long qu, uint32_t hu, int32_t u, long long qv,
+                                        uint32_t hv, int32_t v) {
+  if (qu != qv) return qu > qv;
+  if (hu != hv) return hu < hv;
+  return u < v;
+}
+
+// --------------------------------------------------------- reductions
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x, unsigned mask = 0xFFFFFFFFu) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
+  return x;
+}
+
+// Sum within aligned groups of G lanes (G a power of two <= 32).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+// Argmax (gain, id) within aligned groups of G lanes.
+template <int G>
+__device__ __forceinline__ void group_argmax(long long &g, int32_t &x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    long long g2 = __shfl_xor_sync(0xFFFFFFFFu, g, o);
+    int32_t x2 = __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    if (better(g2, x2, g, x)) {
+      g = g2;
+      x = x2;
+    }
+  }
+}
+
+// ------------------------------------------------------------- launch
+
+inline int grid_for(int64_t work, int per_block, int cap = 152 * 32) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace lc

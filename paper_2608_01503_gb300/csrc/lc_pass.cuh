@@ -1,0 +1,52 @@
+// lc_pass.cuh — launch interface of the local-move pass kernels (lc_pass.cu).
+#pragma once
+
+#include "lc_internal.cuh"
+
+namespace lc {
+
+// Everything one pass kernel reads or writes (device pointers, by value).
+struct PassArgs {
+  LevelGraph g;
+  Method m;
+  int32_t *C;       // clustering entering the pass (updated by the apply step)
+  int64_t *W;       // W(X) for X in [0, n)
+  int32_t *D;       // destination of candidates; kNone for non-candidates
+  int64_t *delta;   // g(v, D[v]) - g(v, C[v]) of candidates
+  int64_t *q;       // epsilon bucket of delta (ordering of Section IV-A-1)
+  uint8_t *M;       // afterburner survivors
+  Scalars *sc;
+  unsigned long long *gtab;  // clean global hash scratch, >= 2 nnz slots
+  int32_t phi_n, phi_d;      // temperature of this pass
+  int32_t decide;            // 0: accumulate the objective only
+};
+
+// Vertex lists of the degree bins of one level (stable: ascending ids).
+struct Bins {
+  int32_t *lists;    // device, n entries, bin after bin
+  int32_t *offs;     // device, kBins + 1 entries
+  const int32_t *list[kBins];
+  int64_t count[kBins];
+};
+
+void configure_kernels();
+// Builds b.lists / b.offs on the stream; the caller copies b.offs to the host
+// and fills b.list / b.count (see finish_bins).
+void build_bins(const LevelGraph &g, Bins &b, int32_t *scan_tmp, cudaStream_t s);
+void finish_bins(Bins &b, const int32_t *h_offs);
+
+void launch_pass_begin(Scalars *sc, cudaStream_t s);
+void launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
+void launch_move(const PassArgs &a, const Bins &b, cudaStream_t s);
+void launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
+void launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
+// Update step: moves, W, then ids for movers to new empty clusters.
+// E: uint8[n], used: int32[n], freelist: int32[n] scratch.
+void launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist,
+                  int32_t *scan_tmp, cudaStream_t s);
+void launch_bestof(Scalars *sc, const int32_t *C, int32_t *C_out, int64_t n, cudaStream_t s);
+void launch_iota(int32_t *C, int64_t n, cudaStream_t s);
+void launch_cluster_weights(const int32_t *C, const int64_t *vw, int64_t *W, int64_t n,
+                            cudaStream_t s);
+
+}  // namespace lc

@@ -1,0 +1,90 @@
+"""The C ABI library loads and exports every symbol include/*.h declares, and
+the Python binding's struct mirrors match the C layouts (CPU only: no
+compute calls)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names += re.findall(r"LC_API\s+[\w\s\*]*?\b(lc_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2608_01503_gb300 as lc
+
+    return lc.load()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ("lc_cluster", "lc_cluster_host", "lc_local_move", "lc_contract", "lc_objective",
+                 "lc_strerror", "lc_default_opts"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", lib._name]).decode()
+    exported = set(re.findall(r"\sT\s(\w+)$", out, re.M))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in declared_symbols():
+        assert hasattr(lib, s)
+
+
+def test_binding_exports_match_header():
+    import paper_2608_01503_gb300 as lc
+
+    assert sorted(lc.EXPORTS) == [s for s in declared_symbols() if s in lc.EXPORTS]
+    for s in declared_symbols():
+        assert hasattr(lc, s) or s == "lc_default_opts", s
+
+
+def test_struct_layouts_match_c(tmp_path):
+    import paper_2608_01503_gb300 as lc
+
+    prog = tmp_path / "sizes.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "lc.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(lc_opts), sizeof(lc_result),"
+        " sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream), offsetof(lc_result, error_detail));"
+        "return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = list(map(int, subprocess.check_output([str(exe)]).split()))
+    assert vals == [ctypes.sizeof(lc._Opts), ctypes.sizeof(lc._Result), ctypes.sizeof(lc._Event),
+                    ctypes.sizeof(lc._Csr), lc._Opts.stream.offset, lc._Result.error_detail.offset]
+
+
+def test_defaults_and_strerror(lib):
+    import paper_2608_01503_gb300 as lc
+
+    o = lc._Opts()
+    lib.lc_default_opts(ctypes.byref(o))
+    assert o.pass_limit == 6 and (o.eps_num, o.eps_den) == (1, 10)
+    assert [(o.phi_num[i], o.phi_den[i]) for i in range(6)] == [(3, 4)] * 4 + [(1, 4)] * 2
+    assert o.uncoarsen == 1 and o.validate == 1
+    assert lc.lc_strerror(0) == "ok"
+    assert "symmetric" in lc.lc_strerror(2)
+
+
+def test_product_path_does_not_reference_oracle():
+    """The CUDA path and its binding never import or load the oracle."""
+    pkg = os.path.join(ROOT, "paper_2608_01503_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "lc_oracle" not in text and "liboracle" not in text, f

@@ -148,6 +148,7 @@ struct Prof {
 struct Level {
   LevelGraph g{};
   Bins bins{};
+  Hubs hub{};
   int32_t *Cd = nullptr;  // dense coarsening clustering of this level
   int64_t n_c = 0;
 };
@@ -162,9 +163,10 @@ struct Run {
   // scratch sized for G_0
   int32_t *C = nullptr, *D = nullptr, *C_out = nullptr, *freelist = nullptr, *used = nullptr,
           *newid = nullptr, *cnt = nullptr, *scan32 = nullptr;
-  int64_t *W = nullptr, *delta = nullptr, *q = nullptr, *bound = nullptr, *off = nullptr,
+  int64_t *W = nullptr, *delta = nullptr, *bound = nullptr, *off = nullptr,
           *scan64 = nullptr;
   uint8_t *M = nullptr, *E = nullptr;
+  AbRec *ab = nullptr;
   unsigned long long *gtab = nullptr;
   Scalars *sc = nullptr, *sc_trace = nullptr;
   GraphStats *st = nullptr;
@@ -183,7 +185,7 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.scan32, scan_scratch(big)));
   LC_TRY(r.ar.get(&r.W, n0));
   LC_TRY(r.ar.get(&r.delta, n0));
-  LC_TRY(r.ar.get(&r.q, n0));
+  LC_TRY(r.ar.get(&r.ab, n0));
   LC_TRY(r.ar.get(&r.bound, n0 + 1));
   LC_TRY(r.ar.get(&r.off, n0 + 1));
   LC_TRY(r.ar.get(&r.scan64, scan_scratch(n0 + 1)));
@@ -197,6 +199,8 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   return LC_OK;
 }
 
+// Degree bins of a level, and the chunk plan of its hub bin (rows longer
+// than the largest shared-memory bin are cut into kHubChunk-edge chunks).
 static int bins_for(Run &r, Level &L) {
   LC_TRY(r.ar.get(&L.bins.lists, L.g.n));
   LC_TRY(r.ar.get(&L.bins.offs, kBins + 1));
@@ -205,36 +209,80 @@ static int bins_for(Run &r, Level &L) {
   LC_CK(cudaMemcpyAsync(h, L.bins.offs, sizeof(h), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
   finish_bins(L.bins, h);
-  r.res->kernel_launches[LC_K_OTHER] += 3 * kBins + kBins;
+  r.res->kernel_launches[LC_K_OTHER] += 4 * kBins;
+  L.hub = Hubs{};
+  const int H = (int)L.bins.count[kHubBin];
+  if (H > 0) {
+    int64_t *rows = nullptr;
+    LC_TRY(r.ar.get(&rows, 2 * H));
+    launch_hub_rows(L.g.rp, L.bins.list[kHubBin], H, rows, r.s);
+    r.res->kernel_launches[LC_K_OTHER] += 1;
+    std::vector<int64_t> hrows(2 * (size_t)H);
+    LC_CK(cudaMemcpyAsync(hrows.data(), rows, 16 * (size_t)H, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaStreamSynchronize(r.s));
+    std::vector<int32_t> hub_of, c0(H + 1);
+    std::vector<int64_t> e0, e1;
+    for (int k = 0; k < H; ++k) {
+      c0[k] = (int32_t)hub_of.size();
+      for (int64_t b = hrows[2 * k]; b < hrows[2 * k + 1]; b += kHubChunk) {
+        hub_of.push_back(k);
+        e0.push_back(b);
+        e1.push_back(b + kHubChunk < hrows[2 * k + 1] ? b + kHubChunk : hrows[2 * k + 1]);
+      }
+    }
+    const int Q = (int)hub_of.size();
+    c0[H] = Q;
+    int32_t *d_hub_of, *d_c0, *d_part_x;
+    int64_t *d_e0, *d_e1;
+    long long *d_acc, *d_part_g;
+    LC_TRY(r.ar.get(&d_hub_of, Q));
+    LC_TRY(r.ar.get(&d_c0, H + 1));
+    LC_TRY(r.ar.get(&d_part_x, Q));
+    LC_TRY(r.ar.get(&d_e0, Q));
+    LC_TRY(r.ar.get(&d_e1, Q));
+    LC_TRY(r.ar.get(&d_acc, H));
+    LC_TRY(r.ar.get(&d_part_g, Q));
+    LC_CK(cudaMemcpyAsync(d_hub_of, hub_of.data(), 4 * (size_t)Q, cudaMemcpyHostToDevice, r.s));
+    LC_CK(cudaMemcpyAsync(d_c0, c0.data(), 4 * (size_t)(H + 1), cudaMemcpyHostToDevice, r.s));
+    LC_CK(cudaMemcpyAsync(d_e0, e0.data(), 8 * (size_t)Q, cudaMemcpyHostToDevice, r.s));
+    LC_CK(cudaMemcpyAsync(d_e1, e1.data(), 8 * (size_t)Q, cudaMemcpyHostToDevice, r.s));
+    LC_CK(cudaMemsetAsync(d_acc, 0, 8 * (size_t)H, r.s));
+    LC_CK(cudaStreamSynchronize(r.s));  // host vectors are released below
+    L.hub.H = H;
+    L.hub.Q = Q;
+    L.hub.vtx = L.bins.list[kHubBin];
+    L.hub.hub_of = d_hub_of;
+    L.hub.e0 = d_e0;
+    L.hub.e1 = d_e1;
+    L.hub.c0 = d_c0;
+    L.hub.acc = d_acc;
+    L.hub.part_g = d_part_g;
+    L.hub.part_x = d_part_x;
+  }
   return launch_check();
 }
 
-static PassArgs pass_args(Run &r, const LevelGraph &g) {
+static PassArgs pass_args(Run &r, const Level &L) {
   PassArgs a{};
-  a.g = g;
+  a.g = L.g;
   a.m = r.m;
   a.C = r.C;
   a.W = r.W;
   a.D = r.D;
   a.delta = r.delta;
-  a.q = r.q;
+  a.ab = r.ab;
   a.M = r.M;
   a.sc = r.sc;
   a.gtab = r.gtab;
-  a.decide = 1;
+  a.hub = L.hub;
   return a;
 }
 
-static int nonempty_bins(const Bins &b) {
-  int k = 0;
-  for (int i = 0; i < kBins; ++i) k += b.count[i] > 0;
-  return k;
-}
 
 // Host copies for the optional trace callback.
 static int emit_pass_event(Run &r, const Level &L, int level, int phase, int pass) {
   const int64_t n = L.g.n;
-  PassArgs a = pass_args(r, L.g);
+  PassArgs a = pass_args(r, L);
   a.sc = r.sc_trace;
   LC_CK(cudaMemsetAsync(r.sc_trace, 0, sizeof(Scalars), r.s));
   launch_objective(a, L.bins, r.s);
@@ -271,8 +319,7 @@ static int emit_pass_event(Run &r, const Level &L, int level, int phase, int pas
 // r.sc->phi_out.
 static int local_move_passes(Run &r, Level &L, bool singleton, int level, int phase) {
   const int64_t n = L.g.n, nnz = L.g.nnz;
-  PassArgs a = pass_args(r, L.g);
-  const double nb = (double)nonempty_bins(L.bins);
+  PassArgs a = pass_args(r, L);
   if (singleton) {
     launch_iota(r.C, n, r.s);
     launch_iota(r.C_out, n, r.s);
@@ -292,37 +339,32 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     launch_pass_begin(r.sc, r.s);
     if (i == 1 && singleton) {
       r.prof.begin(LC_K_FIRST_PASS);
-      launch_first_pass(a, L.bins, r.s);
+      r.res->kernel_launches[LC_K_FIRST_PASS] += launch_first_pass(a, L.bins, r.s);
       r.prof.end(16.0 * nnz + 44.0 * n);
-      r.res->kernel_launches[LC_K_FIRST_PASS] += (int64_t)nb;
     } else {
       r.prof.begin(LC_K_MOVE);
-      launch_move(a, L.bins, r.s);
+      r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
       r.prof.end(12.0 * nnz + 48.0 * n);
-      r.res->kernel_launches[LC_K_MOVE] += (int64_t)nb;
       r.prof.begin(LC_K_APPLY);
       launch_bestof(r.sc, r.C, r.C_out, n, r.s);
       r.prof.end(8.0 * n);
       r.res->kernel_launches[LC_K_APPLY] += 2;
     }
     r.prof.begin(LC_K_AFTERBURNER);
-    launch_afterburner(a, L.bins, r.s);
+    r.res->kernel_launches[LC_K_AFTERBURNER] += launch_afterburner(a, L.bins, r.s);
     r.prof.end(5.0 * n);
-    r.res->kernel_launches[LC_K_AFTERBURNER] += (int64_t)nb;
     r.prof.begin(LC_K_APPLY);
-    launch_apply(a, r.E, r.used, r.freelist, r.scan32, r.s);
+    r.res->kernel_launches[LC_K_APPLY] += launch_apply(a, r.E, r.used, r.freelist, r.scan32, r.s);
     r.prof.end(14.0 * n);
-    r.res->kernel_launches[LC_K_APPLY] += 9;
     LC_TRY(launch_check());
     r.res->passes_total++;
     r.res->edges_local_move += nnz;
     if (r.o.event_cb) LC_TRY(emit_pass_event(r, L, level, phase, i));
   }
   r.prof.begin(LC_K_OBJECTIVE);
-  launch_objective(a, L.bins, r.s);
+  r.res->kernel_launches[LC_K_OBJECTIVE] += launch_objective(a, L.bins, r.s) + 2;
   launch_bestof(r.sc, r.C, r.C_out, n, r.s);
   r.prof.end(12.0 * nnz + 32.0 * n);
-  r.res->kernel_launches[LC_K_OBJECTIVE] += (int64_t)nb + 2;
   LC_TRY(launch_check());
   if (r.o.event_cb) {
     std::vector<int32_t> C(n > 0 ? n : 1);
@@ -368,8 +410,8 @@ static int contract_level(Run &r, Level &L, Level &N, int level) {
   LC_TRY(r.ar.get(&vw_c, n_c));
   r.prof.begin(LC_K_CONTRACT);
   launch_contract_offsets(L.g, L.Cd, n_c, r.bound, r.off, vw_c, r.scan64, r.s);
-  launch_contract_insert(L.g, L.Cd, r.off, r.gtab, r.cnt, n_c, &r.sc->error, L.bins.list,
-                         L.bins.count, r.s);
+  const int ni = launch_contract_insert(L.g, L.Cd, r.off, r.gtab, r.cnt, n_c, &r.sc->error,
+                                       L.bins.list, L.bins.count, L.hub, r.s);
   launch_contract_rowptr(r.cnt, n_c, rp_c, r.scan64, r.s);
   r.prof.end(16.0 * L.g.nnz + 48.0 * L.g.n);
   int64_t nnz_c = 0;
@@ -382,7 +424,7 @@ static int contract_level(Run &r, Level &L, Level &N, int level) {
   r.prof.begin(LC_K_CONTRACT);
   launch_contract_compact(r.gtab, 2 * L.g.nnz, col_c, ew_c, r.scan32, r.s);
   r.prof.end(16.0 * L.g.nnz + 8.0 * nnz_c);
-  r.res->kernel_launches[LC_K_CONTRACT] += 12 + nonempty_bins(L.bins);
+  r.res->kernel_launches[LC_K_CONTRACT] += 11 + ni;
   LC_TRY(launch_check());
   r.res->edges_contract += L.g.nnz;
   N.g.n = n_c;
@@ -446,14 +488,15 @@ static int prepare(Run &r, const LevelGraph &g, GraphStats *hst) {
   int64_t ends[2] = {0, 0};
   LC_CK(cudaMemcpyAsync(&ends[0], g.rp, 8, cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaMemcpyAsync(&ends[1], g.rp + g.n, 8, cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  if (ends[0] != 0 || ends[1] != g.nnz) return LC_ERR_ARG;
   r.prof.begin(LC_K_OTHER);
   launch_stats(g, r.o.validate, r.st, r.s);
   r.prof.end(16.0 * g.n + 8.0 * g.nnz);
-  r.res->kernel_launches[LC_K_OTHER] += 1;
+  r.res->kernel_launches[LC_K_OTHER] += g.nnz > 0 ? 2 : 1;
   LC_CK(cudaMemcpyAsync(hst, r.st, sizeof(GraphStats), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
   LC_TRY(launch_check());
-  if (ends[0] != 0 || ends[1] != g.nnz) return LC_ERR_ARG;
   if (r.o.validate) {
     if (hst->err_key != ~0ull) {
       r.res->error_detail = (int64_t)(hst->err_key & 0xFFFFFFFFFFull);
@@ -493,12 +536,11 @@ static int objective_of(Run &r, Level &L, const int32_t *labels, long long *phi)
   const int64_t n = L.g.n;
   LC_CK(cudaMemcpyAsync(r.C, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
   launch_cluster_weights(r.C, L.g.vw, r.W, n, r.s);
-  PassArgs a = pass_args(r, L.g);
+  PassArgs a = pass_args(r, L);
   LC_CK(cudaMemsetAsync(r.sc, 0, sizeof(Scalars), r.s));
   r.prof.begin(LC_K_OBJECTIVE);
-  launch_objective(a, L.bins, r.s);
+  r.res->kernel_launches[LC_K_OBJECTIVE] += launch_objective(a, L.bins, r.s) + 1;
   r.prof.end(12.0 * L.g.nnz + 32.0 * n);
-  r.res->kernel_launches[LC_K_OBJECTIVE] += nonempty_bins(L.bins) + 1;
   LC_CK(cudaMemcpyAsync(phi, &r.sc->phi_acc, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
   return launch_check();
@@ -783,7 +825,7 @@ int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
     L.n_c = n_c;
     launch_contract_offsets(L.g, L.Cd, n_c, r.bound, r.off, c_vw, r.scan64, r.s);
     launch_contract_insert(L.g, L.Cd, r.off, r.gtab, r.cnt, n_c, &r.sc->error, L.bins.list,
-                           L.bins.count, r.s);
+                           L.bins.count, L.hub, r.s);
     launch_contract_rowptr(r.cnt, n_c, c_row_ptr, r.scan64, r.s);
     int64_t nnz_c = 0;
     if (cudaMemcpyAsync(&nnz_c, c_row_ptr + n_c, 8, cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||

@@ -70,7 +70,42 @@ struct InsertArgs {
   int *error;
 };
 
-// Insert every fine edge of v leaving C[v] into the coarse table of C[v].
+// Insert fine edges [e0, e1) of v leaving C[v] into the coarse table of
+// x = C[v] (strided by GS, loads batched U at a time); returns the number of
+// slots this thread claimed.
+template <int GS>
+__device__ __forceinline__ int insert_edges(const InsertArgs &a, int32_t x, int64_t e0, int64_t e1,
+                                            int r, bool &ok) {
+  constexpr int U = 4;
+  const int64_t o0 = a.off[x];
+  const uint32_t cap = (uint32_t)(2 * (a.off[x + 1] - o0));
+  unsigned long long *tab = a.tab + 2 * o0;
+  int fresh_n = 0;
+  for (int64_t base = e0; base < e1; base += (int64_t)GS * U) {
+    int32_t u[U], w[U], y[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t e = base + k * GS + r;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < e1) {
+        u[k] = __ldg(a.g.col + e);
+        w[k] = __ldg(a.g.ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) y[k] = u[k] >= 0 ? a.Cd[u[k]] : x;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (y[k] == x) continue;
+      bool fresh = false;
+      ok &= table_add(tab, cap, y[k], w[k], fresh);
+      fresh_n += fresh;
+    }
+  }
+  return fresh_n;
+}
+
 template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     k_insert(InsertArgs a, const int32_t *__restrict__ list, int64_t count) {
@@ -79,22 +114,22 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     if (!active) return;
     const int32_t v = list[i];
     const int32_t x = a.Cd[v];
-    const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
-    const int64_t o0 = a.off[x];
-    const uint32_t cap = (uint32_t)(2 * (a.off[x + 1] - o0));
-    unsigned long long *tab = a.tab + 2 * o0;
-    int fresh_n = 0;
     bool ok = true;
-    for (int64_t e = beg + r; e < end; e += GS) {
-      const int32_t y = a.Cd[__ldg(a.g.col + e)];
-      if (y == x) continue;
-      bool fresh = false;
-      ok &= table_add(tab, cap, y, __ldg(a.g.ew + e), fresh);
-      fresh_n += fresh;
-    }
+    const int fresh_n = insert_edges<GS>(a, x, a.g.rp[v], a.g.rp[v + 1], r, ok);
     if (!ok) *a.error = 1;
     if (fresh_n) atomicAdd(&a.cnt[x], fresh_n);
   });
+}
+
+// Hub rows: one block per chunk of kHubChunk edges.
+__global__ void __launch_bounds__(kHubThreads) k_insert_hub(InsertArgs a, Hubs hub) {
+  const int c = blockIdx.x;
+  const int32_t v = hub.vtx[hub.hub_of[c]];
+  const int32_t x = a.Cd[v];
+  bool ok = true;
+  const int fresh_n = insert_edges<kHubThreads>(a, x, hub.e0[c], hub.e1[c], threadIdx.x, ok);
+  if (!ok) *a.error = 1;
+  if (fresh_n) atomicAdd(&a.cnt[x], fresh_n);
 }
 
 struct CntIn {
@@ -157,23 +192,36 @@ void launch_contract_offsets(const LevelGraph &g, const int32_t *Cd, int64_t n_c
 }
 
 template <int GS>
-static void launch_insert(const InsertArgs &a, const int32_t *list, int64_t count, cudaStream_t s) {
-  if (count <= 0) return;
+static int launch_insert(const InsertArgs &a, const int32_t *list, int64_t count, cudaStream_t s) {
+  if (count <= 0) return 0;
   const int threads = GS > 32 ? GS : 256;
   const int per_block = GS > 32 ? 1 : threads / GS;
   k_insert<GS><<<blocks_for(count, per_block), threads, 0, s>>>(a, list, count);
+  return 1;
 }
 
-void launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t *off,
-                            unsigned long long *tab, int32_t *cnt, int64_t n_c, int *error,
-                            const int32_t *const *lists, const int64_t *counts, cudaStream_t s) {
+int launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t *off,
+                           unsigned long long *tab, int32_t *cnt, int64_t n_c, int *error,
+                           const int32_t *const *lists, const int64_t *counts, const Hubs &hub,
+                           cudaStream_t s) {
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n_c > 0 ? n_c : 1), s);
   InsertArgs a{g, Cd, off, tab, cnt, error};
-  launch_insert<8>(a, lists[0], counts[0], s);
-  launch_insert<32>(a, lists[1], counts[1], s);
-  launch_insert<32>(a, lists[2], counts[2], s);
-  launch_insert<kBin3Threads>(a, lists[3], counts[3], s);
-  launch_insert<kBin4Threads>(a, lists[4], counts[4], s);
+  auto range = [&](int lo, int hi) {
+    int64_t c = 0;
+    for (int k = lo; k <= hi; ++k) c += counts[k];
+    return c;
+  };
+  int n = 0;
+  n += launch_insert<1>(a, lists[0], range(0, 0), s);
+  n += launch_insert<16>(a, lists[1], range(1, 1), s);
+  n += launch_insert<32>(a, lists[2], range(2, 4), s);
+  n += launch_insert<128>(a, lists[5], range(5, 6), s);
+  n += launch_insert<512>(a, lists[7], range(7, 8), s);
+  if (hub.H > 0) {
+    k_insert_hub<<<hub.Q, kHubThreads, 0, s>>>(a, hub);
+    n++;
+  }
+  return n;
 }
 
 void launch_contract_rowptr(const int32_t *cnt, int64_t n_c, int64_t *rp_c, int64_t *scan_tmp64,

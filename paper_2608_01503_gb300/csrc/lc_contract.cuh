@@ -16,9 +16,11 @@ const int32_t *compact_total(const int32_t *scan_tmp, int64_t n);
 void launch_contract_offsets(const LevelGraph &g, const int32_t *Cd, int64_t n_c, int64_t *bound,
                              int64_t *off, int64_t *vw_c, int64_t *scan_tmp64, cudaStream_t s);
 // Algorithm 4, lines 5-12: inserts with unique counting (cnt int32[n_c]).
-void launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t *off,
-                            unsigned long long *tab, int32_t *cnt, int64_t n_c, int *error,
-                            const int32_t *const *lists, const int64_t *counts, cudaStream_t s);
+// Returns the number of kernels launched.
+int launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t *off,
+                           unsigned long long *tab, int32_t *cnt, int64_t n_c, int *error,
+                           const int32_t *const *lists, const int64_t *counts, const Hubs &hub,
+                           cudaStream_t s);
 // Coarse row offsets from the unique counts; rp_c[n_c] = nnz_c.
 void launch_contract_rowptr(const int32_t *cnt, int64_t n_c, int64_t *rp_c, int64_t *scan_tmp64,
                             cudaStream_t s);

@@ -21,18 +21,28 @@ constexpr unsigned long long kEmptySlot = 0ull;
 constexpr int kMaxLevels = 256;
 
 // Degree bins of the per-vertex kernels.  A vertex of degree d is handled by
-//   bin 0: d <= 8       a group of 8 lanes (4 vertices per warp), one neighbour per lane
-//   bin 1: d <= 32      one warp, one neighbour per lane
-//   bin 2: d <= 256     one warp; aggregation in a shared-memory table of <= 512 slots
-//   bin 3: d <= 4096    one 256-thread block; shared-memory table of <= 8192 slots
-//   bin 4: d >  4096    one 512-thread block; global-memory table of 2d slots
-constexpr int kBins = 5;
-constexpr int64_t kBinMaxDeg[kBins - 1] = {8, 32, 256, 4096};
-constexpr int kBin2Warps = 8;        // warps per block in bin 2
-constexpr int kBin2Slots = 512;      // table slots per warp in bin 2
-constexpr int kBin3Threads = 256;
-constexpr int kBin3Slots = 8192;
-constexpr int kBin4Threads = 512;
+//   bin 0: d <= 8       one thread (aggregation in registers)
+//   bin 1: d <= 16      16 lanes, one neighbour per lane (2 vertices per warp)
+//   bin 2: d <= 32      one warp, one neighbour per lane
+//   bin 3: d <= 128     one warp, shared table of 256 slots
+//   bin 4: d <= 256     one warp, shared table of 512 slots
+//   bin 5: d <= 512     64 threads, shared table of 1024 slots
+//   bin 6: d <= 1024    128 threads, shared table of 2048 slots
+//   bin 7: d <= 2048    256 threads, shared table of 4096 slots
+//   bin 8: d <= 4096    256 threads, shared table of 8192 slots
+//   bin 9: d >  4096    "hubs": the row is cut into chunks of kHubChunk edges
+//                       processed by independent blocks, aggregation in the
+//                       vertex's region of the global table (2d slots), then
+//                       one finalize step per hub
+// A vertex's table holds 2d slots at most, so the shared memory a bin
+// reserves per vertex tracks its degree and many vertices stay in flight.
+// Kernels without tables launch once over a contiguous range of bins.
+constexpr int kBins = 10;
+constexpr int kHubBin = kBins - 1;
+constexpr int64_t kBinMaxDeg[kBins - 1] = {8, 16, 32, 128, 256, 512, 1024, 2048, 4096};
+constexpr int kWarpBinWarps = 8;    // warps per block in the warp-table bins
+constexpr int kHubThreads = 256;
+constexpr int kHubChunk = 2048;     // edges per hub chunk
 
 // One level's graph G_l (device pointers).
 struct LevelGraph {
@@ -43,6 +53,19 @@ struct LevelGraph {
   const int64_t *vw;
 };
 
+// Hub chunks of one level (bin 6).  Chunk c covers edges [e0[c], e1[c]) of
+// hub hub_of[c]; the chunks of hub h are [c0[h], c0[h+1]).
+struct Hubs {
+  int32_t H = 0, Q = 0;
+  const int32_t *vtx = nullptr;     // [H] hub vertex ids
+  const int32_t *hub_of = nullptr;  // [Q]
+  const int64_t *e0 = nullptr, *e1 = nullptr;  // [Q]
+  const int32_t *c0 = nullptr;      // [H+1]
+  long long *acc = nullptr;         // [H] per-hub sums, zero between uses
+  long long *part_g = nullptr;      // [Q] per-chunk argmax partials
+  int32_t *part_x = nullptr;        // [Q]
+};
+
 // Method constants of one call.
 struct Method {
   int64_t mu, Lam;        // lambda = mu / Lam
@@ -50,16 +73,11 @@ struct Method {
   uint32_t seed;
 };
 
-// Per-pass arrays (device), all of length n of the current level.
-struct PassState {
-  int32_t *C;       // current clustering, values in [0, n)
-  int64_t *W;       // W(X) per label X in [0, n)
-  int32_t *D;       // destination for candidates, kNone otherwise
-  int64_t *delta;   // g(v,D[v]) - g(v,C[v]) for candidates
-  int64_t *q;       // epsilon bucket of delta for candidates
-  uint8_t *M;       // afterburner survivors
-  int32_t *C_out;   // best clustering seen
-  // scalars (device), see Scalars below
+// Afterburner record of a vertex for one pass: its cluster, destination and
+// priority bucket packed into one 16-byte load.
+struct __align__(16) AbRec {
+  int32_t C, D;
+  long long q;
 };
 
 // Device-resident scalars of one LocalMovePasses call.
@@ -103,9 +121,9 @@ __device__ __forceinline__ int32_t slot_val(unsigned long long s) { return (int3
 // word (values stay below 2^31, so the add never carries into the key).
 // Returns false when all `cap` slots were probed without success, a bound
 // violation (every caller sizes tables to at least twice its distinct keys).
-// `fresh` is set when this call claimed a new slot.
+// When this call claimed a new slot, `fresh` is set and `slot` names it.
 __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap, int32_t key,
-                                          int32_t w, bool &fresh) {
+                                          int32_t w, bool &fresh, uint32_t &slot) {
   const unsigned long long tag = (unsigned long long)((uint32_t)key + 1u) << 32;
   uint32_t s = slot_of(key, cap);
   for (uint32_t probe = 0; probe < cap; ++probe) {
@@ -114,6 +132,7 @@ __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap,
       unsigned long long prev = atomicCAS(&tab[s], kEmptySlot, tag | (uint32_t)w);
       if (prev == kEmptySlot) {
         fresh = true;
+        slot = s;
         return true;
       }
       cur = prev;
@@ -125,6 +144,12 @@ __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap,
     s = (s + 1 == cap) ? 0 : s + 1;
   }
   return false;
+}
+
+__device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap, int32_t key,
+                                          int32_t w, bool &fresh) {
+  uint32_t slot;
+  return table_add(tab, cap, key, w, fresh, slot);
 }
 
 // --------------------------------------------------------------- gains

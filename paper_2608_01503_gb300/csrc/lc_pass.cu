@@ -1,10 +1,15 @@
 // lc_pass.cu — kernels of one synchronous local-move pass (Algorithm 2 with
 // the afterburner filter of Algorithm 3) and the per-level objective.
 //
-// Every vertex is handled by a group of threads sized to its degree bin (see
-// kBinMaxDeg): 8 or 32 lanes holding one neighbour each, a warp, or a block.
+// Every vertex is handled by a thread group sized to its degree bin (see
+// kBinMaxDeg in lc_internal.cuh).  The kernels are bound by the latency of
+// dependent gathers (row offsets -> neighbours -> their clusters -> cluster
+// weights), so each group issues its loads in batches before using them, and
+// the bins keep many vertices in flight per SM.  Rows above 4096 entries
+// ("hubs") are cut into chunks processed by independent blocks.
+//
 // All sums are integer (commutative atomics and shuffles), argmax ties go to
-// the smallest cluster id, and the afterburner order is a total order, so
+// the smallest cluster id and the afterburner order is a total order, so the
 // results do not depend on scheduling.
 #include <climits>
 
@@ -17,9 +22,10 @@ namespace lc {
 
 // ---------------------------------------------------- vertex decision
 
-// Algorithm 2 for one vertex once S(v, C[v]) and the best other cluster
+// Algorithm 2 for one vertex once g(v, C[v]) and the best other cluster
 // (gbest, best) are known: the empty-cluster rule, the candidate test with
-// temperature phi = phi_n / phi_d, and the afterburner priority.
+// temperature phi = phi_n / phi_d, and delta_v (Algorithm 3's priority; its
+// epsilon bucket is computed by k_ab_prep, off this latency-bound path).
 __device__ __forceinline__ void decide(const PassArgs &a, int32_t v, long long gC, int32_t best,
                                        long long gbest, long long &cntL) {
   if (gC < 0 && (best == kNone || gbest < 0)) {
@@ -29,10 +35,8 @@ __device__ __forceinline__ void decide(const PassArgs &a, int32_t v, long long g
   const bool inL = best != kNone &&
                    (__int128)a.phi_d * gbest >= (__int128)(a.phi_d - a.phi_n) * (__int128)gC;
   if (inL) {
-    const long long d = gbest - gC;
     a.D[v] = best;
-    a.delta[v] = d;
-    a.q[v] = eps_bucket(a.m, d);
+    a.delta[v] = gbest - gC;
     cntL++;
   } else {
     a.D[v] = kNone;
@@ -44,6 +48,16 @@ __device__ __forceinline__ void decide(const PassArgs &a, int32_t v, long long g
 // Singleton start: the adjacent clusters of v are its neighbours, so the
 // gains are read straight from the CSR: g(v,{u}) = Lam*w(u,v) - mu*w(v)*w(u),
 // and g(v, C[v]) = 0.
+__device__ __forceinline__ void first_edge(const PassArgs &a, int64_t e, long long wv, long long &gb,
+                                           int32_t &xb) {
+  const int32_t u = __ldg(a.g.col + e);
+  const long long g = a.m.Lam * (long long)__ldg(a.g.ew + e) - a.m.mu * wv * __ldg(a.g.vw + u);
+  if (better(g, u, gb, xb)) {
+    gb = g;
+    xb = u;
+  }
+}
+
 template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     k_first_pass(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
@@ -57,21 +71,80 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     const long long wv = active ? a.g.vw[v] : 0;
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    for (int64_t e = beg + r; e < end; e += GS) {
-      const int32_t u = __ldg(a.g.col + e);
-      const long long g = a.m.Lam * (long long)__ldg(a.g.ew + e) - a.m.mu * wv * __ldg(a.g.vw + u);
-      if (better(g, u, gb, xb)) {
-        gb = g;
-        xb = u;
-      }
-    }
+#pragma unroll 4
+    for (int64_t e = beg + r; e < end; e += GS) first_edge(a, e, wv, gb, xb);
     Grp<GS>::argmax(gb, xb, rg, rx);
     if (active && r == 0) decide(a, v, 0, xb, gb, cntL);
   });
   flush_block_sum(cntL, &a.sc->count_L);
 }
 
-// --------------------------------------- aggregation + argmax, bins 0-1
+// ----------------------------------- aggregation + argmax, bin 0 (thread)
+
+// One thread per vertex of degree <= 8: neighbour clusters and weights are
+// held in registers; S(v, X) for each distinct X is an unrolled compare-sum.
+__global__ void __launch_bounds__(256) k_move_thread(PassArgs a, const int32_t *__restrict__ list,
+                                                     int64_t count) {
+  constexpr int K = 8;
+  long long cntL = 0, phi = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[i];
+    const int64_t beg = a.g.rp[v];
+    const int deg = (int)(a.g.rp[v + 1] - beg);
+    const int32_t Cv = a.C[v];
+    const long long wv = a.g.vw[v];
+    int32_t u[K], w[K], X[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      u[j] = 0;
+      w[j] = 0;
+      if (j < deg) {
+        u[j] = __ldg(a.g.col + beg + j);
+        w[j] = __ldg(a.g.ew + beg + j);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) X[j] = j < deg ? a.C[u[j]] : -1;
+    const long long WC = a.W[Cv];
+    long long WX[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) WX[j] = (j < deg && X[j] != Cv) ? a.W[X[j]] : 0;
+    long long self = 0, gb = LLONG_MIN;
+    int32_t xb = kNone;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (j >= deg) continue;
+      if (X[j] == Cv) {
+        self += w[j];
+        continue;
+      }
+      bool first = true;
+      long long S = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (k < deg && X[k] == X[j]) {
+          S += w[k];
+          if (k < j) first = false;
+        }
+      }
+      if (first) {
+        const long long g = gain_other(a.m, S, wv, WX[j]);
+        if (better(g, X[j], gb, xb)) {
+          gb = g;
+          xb = X[j];
+        }
+      }
+    }
+    const long long gC = gain_self(a.m, self, wv, WC);
+    phi += gC;
+    decide(a, v, gC, xb, gb, cntL);
+  }
+  flush_block_sum(cntL, &a.sc->count_L);
+  flush_block_sum(phi, &a.sc->phi_acc);
+}
+
+// ------------------------------------ aggregation + argmax, bins 1-2 (lanes)
 
 // Each lane holds one neighbour; lanes of a group with the same neighbour
 // cluster are matched with __match_any_sync and their weights summed in a
@@ -89,6 +162,7 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
     const int32_t v = active ? list[i] : 0;
     const int64_t beg = active ? a.g.rp[v] : 0, deg = active ? a.g.rp[v + 1] - beg : 0;
     const int32_t Cv = active ? a.C[v] : 0;
+    const long long wv = active ? a.g.vw[v] : 0;
     const bool has = sub < deg;
     int32_t X = -1, w = 0;
     if (has) {
@@ -96,8 +170,10 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
       w = __ldg(a.g.ew + beg + sub);
       X = a.C[u];
     }
+    const long long WC = (active && sub == 0) ? a.W[Cv] : 0;
     const bool self = has && X == Cv;
     const bool other = has && !self;
+    const long long WX = other ? a.W[X] : 0;
     const long long S_self = group_sum<G>((long long)(self ? w : 0));
     const unsigned long long key =
         other ? (((unsigned long long)(lane / G) << 32) | (uint32_t)X) : (0xFFFFFFFF00000000ull | lane);
@@ -107,19 +183,17 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
     __syncwarp();
     if (other) atomicAdd(&acc[wbase + leader], w);
     __syncwarp();
-    long long wv = 0;
-    if (active) wv = a.g.vw[v];
     long long g = LLONG_MIN;
     int32_t x = kNone;
     if (other && lane == leader) {
-      g = gain_other(a.m, acc[threadIdx.x], wv, a.W[X]);
+      g = gain_other(a.m, acc[threadIdx.x], wv, WX);
       x = X;
     }
     group_argmax<G>(g, x);
     if (active && sub == 0) {
-      const long long gC = gain_self(a.m, S_self, wv, a.W[Cv]);
+      const long long gC = gain_self(a.m, S_self, wv, WC);
       phi += gC;
-      if (a.decide) decide(a, v, gC, x, g, cntL);
+      decide(a, v, gC, x, g, cntL);
     }
     __syncwarp();
   });
@@ -127,59 +201,160 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
   flush_block_sum(phi, &a.sc->phi_acc);
 }
 
-// ------------------------------------------ aggregation + argmax, bin 2
+// ------------------------------------ shared-table aggregation, bins 3-5
 
-// One warp per vertex; a per-warp shared table of cap = pow2 >= 2 deg slots.
-__global__ void __launch_bounds__(kBin2Warps * 32)
+// Shared tables stay clean between vertices: each vertex records the slots
+// it claims in a list, and its argmax walks that list (the distinct
+// neighbour clusters only) and resets those slots.  Capacity is 2 deg
+// rounded up to 32, so the load factor is at most 1/2.
+__device__ __forceinline__ uint32_t table_cap(int64_t deg) {
+  return (uint32_t)((2 * deg + 31) & ~31ll);
+}
+
+// Inserts edges [beg, end) of v (strided by GS, loads batched U at a time)
+// into `tab`; claimed slots are appended to `list` (counter `nlist`).
+// Returns this thread's part of S(v, C[v]).
+template <int GS, int U>
+__device__ __forceinline__ long long table_insert_row(const PassArgs &a, int64_t beg, int64_t end,
+                                                      int32_t Cv, unsigned long long *tab,
+                                                      uint32_t cap, uint16_t *list, int *nlist,
+                                                      int r, bool &ok) {
+  long long self = 0;
+  for (int64_t base = beg; base < end; base += GS * U) {
+    int32_t u[U], w[U], X[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t e = base + k * GS + r;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < end) {
+        u[k] = __ldg(a.g.col + e);
+        w[k] = __ldg(a.g.ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (u[k] < 0) continue;
+      if (X[k] == Cv) {
+        self += w[k];
+      } else {
+        bool fresh = false;
+        uint32_t slot = 0;
+        ok &= table_add(tab, cap, X[k], w[k], fresh, slot);
+        if (fresh) list[atomicAdd(nlist, 1)] = (uint16_t)slot;
+      }
+    }
+  }
+  return self;
+}
+
+// Best (gain, cluster) over the claimed slots list[0 .. n) (strided by GS);
+// resets every slot it reads.
+template <int GS>
+__device__ __forceinline__ void list_argmax(const PassArgs &a, unsigned long long *tab,
+                                            const uint16_t *list, int n, long long wv, int r,
+                                            long long &gb, int32_t &xb) {
+  constexpr int U = 4;
+  for (int base = 0; base < n; base += GS * U) {
+    unsigned long long t[U];
+    long long WX[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int i = base + k * GS + r;
+      t[k] = kEmptySlot;
+      if (i < n) {
+        const uint32_t s = list[i];
+        t[k] = tab[s];
+        tab[s] = kEmptySlot;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) WX[k] = t[k] != kEmptySlot ? a.W[slot_key(t[k])] : 0;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (t[k] == kEmptySlot) continue;
+      const int32_t X = slot_key(t[k]);
+      const long long g = gain_other(a.m, slot_val(t[k]), wv, WX[k]);
+      if (better(g, X, gb, xb)) {
+        gb = g;
+        xb = X;
+      }
+    }
+  }
+}
+
+// Best (gain, cluster) over slots [s0, s1) of a global table (strided by
+// GS), resetting the slots it reads (hub chunks).
+template <int GS>
+__device__ __forceinline__ void range_argmax(const PassArgs &a, unsigned long long *tab, uint32_t s0,
+                                             uint32_t s1, long long wv, int r, long long &gb,
+                                             int32_t &xb) {
+  constexpr int U = 4;
+  for (uint32_t base = s0; base < s1; base += GS * U) {
+    unsigned long long t[U];
+    long long WX[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const uint32_t s = base + k * GS + r;
+      t[k] = s < s1 ? tab[s] : kEmptySlot;
+      if (t[k] != kEmptySlot) tab[s] = kEmptySlot;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) WX[k] = t[k] != kEmptySlot ? a.W[slot_key(t[k])] : 0;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (t[k] == kEmptySlot) continue;
+      const int32_t X = slot_key(t[k]);
+      const long long g = gain_other(a.m, slot_val(t[k]), wv, WX[k]);
+      if (better(g, X, gb, xb)) {
+        gb = g;
+        xb = X;
+      }
+    }
+  }
+}
+
+// Bins 3-4: one warp per vertex, a per-warp shared table of SLOTS slots
+// and its claimed-slot list.
+template <int SLOTS>
+__global__ void __launch_bounds__(kWarpBinWarps * 32)
     k_move_warp(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
-  __shared__ unsigned long long tabs[kBin2Warps][kBin2Slots];
+  constexpr int U = SLOTS / 64;  // one batch of loads covers the largest row of the bin
+  __shared__ unsigned long long tabs[kWarpBinWarps][SLOTS];
+  __shared__ uint16_t lists[kWarpBinWarps][SLOTS / 2];
+  __shared__ int nlists[kWarpBinWarps];
   long long cntL = 0, phi = 0;
-  const int lane = threadIdx.x & 31;
-  unsigned long long *tab = tabs[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long *tab = tabs[wid];
+  for (int s = lane; s < SLOTS; s += 32) tab[s] = kEmptySlot;
+  if (lane == 0) nlists[wid] = 0;
+  __syncwarp();
   for_each_vertex<32>(count, [&](int64_t i, bool active) {
     if (!active) return;  // warp-uniform: the whole warp shares i
     const int32_t v = list[i];
     const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
     const int32_t Cv = a.C[v];
-    uint32_t cap = 64;
-    while (cap < 2 * (end - beg)) cap <<= 1;
-    for (uint32_t s = lane; s < cap; s += 32) tab[s] = kEmptySlot;
-    __syncwarp();
-    long long self = 0;
-    bool ok = true;
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      const int32_t u = __ldg(a.g.col + e);
-      const int32_t w = __ldg(a.g.ew + e);
-      const int32_t X = a.C[u];
-      if (X == Cv) {
-        self += w;
-      } else {
-        bool fresh = false;
-        ok &= table_add(tab, cap, X, w, fresh);
-      }
-    }
-    if (!ok) a.sc->error = 1;
-    __syncwarp();
     const long long wv = a.g.vw[v];
+    const uint32_t cap = table_cap(end - beg);
+    bool ok = true;
+    long long self =
+        table_insert_row<32, U>(a, beg, end, Cv, tab, cap, lists[wid], &nlists[wid], lane, ok);
+    if (!ok) a.sc->error = 1;
+    const long long WC = lane == 0 ? a.W[Cv] : 0;
+    __syncwarp();
+    const int nl = nlists[wid];
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    for (uint32_t s = lane; s < cap; s += 32) {
-      const unsigned long long t = tab[s];
-      if (t != kEmptySlot) {
-        const int32_t X = slot_key(t);
-        const long long g = gain_other(a.m, slot_val(t), wv, a.W[X]);
-        if (better(g, X, gb, xb)) {
-          gb = g;
-          xb = X;
-        }
-      }
-    }
+    list_argmax<32>(a, tab, lists[wid], nl, wv, lane, gb, xb);
     group_argmax<32>(gb, xb);
     self = warp_sum(self);
     if (lane == 0) {
-      const long long gC = gain_self(a.m, self, wv, a.W[Cv]);
+      nlists[wid] = 0;
+      const long long gC = gain_self(a.m, self, wv, WC);
       phi += gC;
-      if (a.decide) decide(a, v, gC, xb, gb, cntL);
+      decide(a, v, gC, xb, gb, cntL);
     }
     __syncwarp();
   });
@@ -187,129 +362,310 @@ __global__ void __launch_bounds__(kBin2Warps * 32)
   flush_block_sum(phi, &a.sc->phi_acc);
 }
 
-// --------------------------------------- aggregation + argmax, bins 3-4
-
-// One block per vertex.  kShared: table in dynamic shared memory (cap = pow2
-// >= 2 deg <= kBin3Slots).  Otherwise the table is the vertex's region
-// [2 rp[v], 2 rp[v+1]) of the global scratch, which is clean on entry and
-// reset to empty while it is read.
-template <int GS, bool kShared>
+// Bins 5-8: one block per vertex; dynamic shared memory holds the table
+// (SLOTS x 8 bytes) followed by the claimed-slot list (SLOTS/2 x 2 bytes).
+template <int GS, int SLOTS>
 __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__restrict__ list,
                                                    int64_t count) {
-  extern __shared__ unsigned long long dyn[];
+  extern __shared__ unsigned long long tab[];
+  uint16_t *claimed = reinterpret_cast<uint16_t *>(tab + SLOTS);
   __shared__ long long rs[GS / 32];
   __shared__ long long rg[GS / 32];
   __shared__ int32_t rx[GS / 32];
+  __shared__ int nlist;
   long long cntL = 0, phi = 0;
-  for_each_vertex<GS>(count, [&](int64_t i, bool) {
+  for (int s = threadIdx.x; s < SLOTS; s += GS) tab[s] = kEmptySlot;
+  if (threadIdx.x == 0) nlist = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int32_t v = list[i];
     const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
     const int32_t Cv = a.C[v];
-    unsigned long long *tab;
-    uint32_t cap;
-    if constexpr (kShared) {
-      cap = 64;
-      while (cap < 2 * (end - beg)) cap <<= 1;
-      tab = dyn;
-      for (uint32_t s = threadIdx.x; s < cap; s += GS) tab[s] = kEmptySlot;
-      __syncthreads();
-    } else {
-      cap = (uint32_t)(2 * (end - beg));
-      tab = a.gtab + 2 * beg;
-    }
-    long long self = 0;
-    bool ok = true;
-    for (int64_t e = beg + threadIdx.x; e < end; e += GS) {
-      const int32_t u = __ldg(a.g.col + e);
-      const int32_t w = __ldg(a.g.ew + e);
-      const int32_t X = a.C[u];
-      if (X == Cv) {
-        self += w;
-      } else {
-        bool fresh = false;
-        ok &= table_add(tab, cap, X, w, fresh);
-      }
-    }
-    if (!ok) a.sc->error = 1;
-    __syncthreads();
     const long long wv = a.g.vw[v];
+    const uint32_t cap = table_cap(end - beg);
+    bool ok = true;
+    long long self =
+        table_insert_row<GS, 8>(a, beg, end, Cv, tab, cap, claimed, &nlist, threadIdx.x, ok);
+    if (!ok) a.sc->error = 1;
+    const long long WC = threadIdx.x == 0 ? a.W[Cv] : 0;
+    __syncthreads();
+    const int nl = nlist;
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    for (uint32_t s = threadIdx.x; s < cap; s += GS) {
-      const unsigned long long t = tab[s];
-      if (t != kEmptySlot) {
-        if constexpr (!kShared) tab[s] = kEmptySlot;
-        const int32_t X = slot_key(t);
-        const long long g = gain_other(a.m, slot_val(t), wv, a.W[X]);
-        if (better(g, X, gb, xb)) {
-          gb = g;
-          xb = X;
-        }
-      }
-    }
+    list_argmax<GS>(a, tab, claimed, nl, wv, threadIdx.x, gb, xb);
     Grp<GS>::argmax(gb, xb, rg, rx);
     self = Grp<GS>::sum(self, rs);
     if (threadIdx.x == 0) {
-      const long long gC = gain_self(a.m, self, wv, a.W[Cv]);
+      nlist = 0;
+      const long long gC = gain_self(a.m, self, wv, WC);
       phi += gC;
-      if (a.decide) decide(a, v, gC, xb, gb, cntL);
+      decide(a, v, gC, xb, gb, cntL);
     }
     __syncthreads();
-  });
+  }
+  flush_block_sum(cntL, &a.sc->count_L);
+  flush_block_sum(phi, &a.sc->phi_acc);
+}
+
+// --------------------------------------------------------- hubs (bin 6)
+
+// Block-wide argmax of (g, x) into the chunk partials.
+__device__ __forceinline__ void hub_part_store(const PassArgs &a, int c, long long gb, int32_t xb) {
+  __shared__ long long rg[kHubThreads / 32];
+  __shared__ int32_t rx[kHubThreads / 32];
+  Grp<kHubThreads>::argmax(gb, xb, rg, rx);
+  if (threadIdx.x == 0) {
+    a.hub.part_g[c] = gb;
+    a.hub.part_x[c] = xb;
+  }
+}
+
+__device__ __forceinline__ void hub_acc_add(const PassArgs &a, int h, long long x) {
+  __shared__ long long rs[kHubThreads / 32];
+  x = Grp<kHubThreads>::sum(x, rs);
+  if (threadIdx.x == 0 && x != 0) atomicAdd((unsigned long long *)&a.hub.acc[h], (unsigned long long)x);
+}
+
+// Move, step 1: insert a chunk of a hub row into the hub's global table.
+// Lanes of a warp holding the same cluster are combined first
+// (__match_any_sync), so a popular cluster costs one global atomic per warp.
+__global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
+  constexpr int U = 4;
+  __shared__ int32_t acc[kHubThreads];
+  const int c = blockIdx.x;
+  const int h = a.hub.hub_of[c];
+  const int32_t v = a.hub.vtx[h];
+  const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
+  const int32_t Cv = a.C[v];
+  unsigned long long *tab = a.gtab + 2 * beg;
+  const uint32_t cap = (uint32_t)(2 * (end - beg));
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  const int64_t e0 = a.hub.e0[c], e1 = a.hub.e1[c];
+  long long self = 0;
+  bool ok = true;
+  for (int64_t base = e0; base < e1; base += kHubThreads * U) {
+    int32_t u[U], w[U], X[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t e = base + k * kHubThreads + threadIdx.x;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < e1) {
+        u[k] = __ldg(a.g.col + e);
+        w[k] = __ldg(a.g.ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const bool other = u[k] >= 0 && X[k] != Cv;
+      if (u[k] >= 0 && X[k] == Cv) self += w[k];
+      const unsigned long long key =
+          other ? (unsigned long long)(uint32_t)X[k] : (0xFFFFFFFF00000000ull | lane);
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+      const int leader = __ffs(peers) - 1;
+      acc[threadIdx.x] = 0;
+      __syncwarp();
+      if (other) atomicAdd(&acc[wbase + leader], w[k]);
+      __syncwarp();
+      if (other && lane == leader) {
+        bool fresh = false;
+        ok &= table_add(tab, cap, X[k], acc[threadIdx.x], fresh);
+      }
+      __syncwarp();
+    }
+  }
+  if (!ok) a.sc->error = 1;
+  hub_acc_add(a, h, self);
+}
+
+// Move, step 2: argmax over the chunk's share of the hub table (reset as read).
+__global__ void __launch_bounds__(kHubThreads) k_hub_move_scan(PassArgs a) {
+  const int c = blockIdx.x;
+  const int h = a.hub.hub_of[c];
+  const int32_t v = a.hub.vtx[h];
+  const int64_t beg = a.g.rp[v];
+  const long long wv = a.g.vw[v];
+  long long gb = LLONG_MIN;
+  int32_t xb = kNone;
+  range_argmax<kHubThreads>(a, a.gtab + 2 * beg, (uint32_t)(2 * (a.hub.e0[c] - beg)),
+                            (uint32_t)(2 * (a.hub.e1[c] - beg)), wv, threadIdx.x, gb, xb);
+  hub_part_store(a, c, gb, xb);
+}
+
+// First pass: argmax over a chunk of a hub row.
+__global__ void __launch_bounds__(kHubThreads) k_hub_first(PassArgs a) {
+  const int c = blockIdx.x;
+  const int32_t v = a.hub.vtx[a.hub.hub_of[c]];
+  const long long wv = a.g.vw[v];
+  long long gb = LLONG_MIN;
+  int32_t xb = kNone;
+#pragma unroll 4
+  for (int64_t e = a.hub.e0[c] + threadIdx.x; e < a.hub.e1[c]; e += kHubThreads)
+    first_edge(a, e, wv, gb, xb);
+  hub_part_store(a, c, gb, xb);
+}
+
+// Final step per hub: combine chunk partials, then decide (Algorithm 2).
+// first = 1: singleton start, g(v, C[v]) = 0 and no objective term.
+__global__ void k_hub_decide(PassArgs a, int first) {
+  long long cntL = 0, phi = 0;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < a.hub.H; h += gridDim.x * blockDim.x) {
+    const int32_t v = a.hub.vtx[h];
+    long long gb = LLONG_MIN;
+    int32_t xb = kNone;
+    for (int c = a.hub.c0[h]; c < a.hub.c0[h + 1]; ++c)
+      if (better(a.hub.part_g[c], a.hub.part_x[c], gb, xb)) {
+        gb = a.hub.part_g[c];
+        xb = a.hub.part_x[c];
+      }
+    long long gC = 0;
+    if (!first) {
+      const long long self = a.hub.acc[h];
+      a.hub.acc[h] = 0;
+      gC = gain_self(a.m, self, a.g.vw[v], a.W[a.C[v]]);
+      phi += gC;
+    }
+    decide(a, v, gC, xb, gb, cntL);
+  }
   flush_block_sum(cntL, &a.sc->count_L);
   flush_block_sum(phi, &a.sc->phi_acc);
 }
 
 // ------------------------------------------------ afterburner (Algorithm 3)
 
+// Packs {C, D, epsilon bucket of delta} per vertex for the afterburner's
+// neighbour gathers (one 16-byte load each).  The bucket of Section IV-A-1,
+// floor(eps_den * delta / (eps_num * Lambda)), needs a 128-bit division; it
+// is done here, one thread per vertex, off the aggregation kernels.
+__global__ void k_ab_prep(PassArgs a) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    AbRec r;
+    r.C = a.C[v];
+    r.D = a.D[v];
+    r.q = r.D != kNone ? eps_bucket(a.m, a.delta[v]) : 0;
+    a.ab[v] = r;
+  }
+}
+
+struct AbCtx {
+  int32_t v, Cv, Dv;
+  long long qv, wv;
+  uint32_t hv;
+};
+
+__device__ __forceinline__ AbCtx ab_ctx(const PassArgs &a, int32_t v) {
+  const AbRec r = a.ab[v];
+  AbCtx c;
+  c.v = v;
+  c.Cv = r.C;
+  c.Dv = r.D;
+  c.qv = r.q;
+  c.wv = a.g.vw[v];
+  c.hv = fmix32((uint32_t)v ^ a.m.seed);
+  return c;
+}
+
+// Sum over edges [e0, e1) (strided by GS, loads batched U at a time) of the
+// change of v's two gains when an adjacent candidate u that precedes v moves
+// from C[u] to D[u] (Algorithm 3's four rules).
+template <int GS, int U>
+__device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c, int64_t e0,
+                                              int64_t e1, int r) {
+  long long d = 0;
+  for (int64_t base = e0; base < e1; base += (int64_t)GS * U) {
+    int32_t u[U], w[U];
+    AbRec rec[U];
+    long long wu[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t e = base + (int64_t)k * GS + r;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < e1) {
+        u[k] = __ldg(a.g.col + e);
+        w[k] = __ldg(a.g.ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      rec[k].D = kNone;
+      if (u[k] >= 0) rec[k] = a.ab[u[k]];
+    }
+    bool need[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      need[k] = rec[k].D != kNone &&
+                earlier(rec[k].q, fmix32((uint32_t)u[k] ^ a.m.seed), u[k], c.qv, c.hv, c.v);
+      wu[k] = need[k] ? a.g.vw[u[k]] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (!need[k]) continue;
+      const long long aw = a.m.Lam * (long long)w[k] - a.m.mu * wu[k] * c.wv;
+      const int32_t Cu = rec[k].C, Du = rec[k].D;
+      if (c.Cv == Cu)
+        d += aw;
+      else if (c.Dv == Cu)
+        d -= aw;
+      if (c.Cv == Du)
+        d -= aw;
+      else if (c.Dv >= 0 && c.Dv == Du)
+        d += aw;
+    }
+  }
+  return d;
+}
+
 // For each candidate v: delta_v adjusted by every adjacent candidate u that
-// precedes v in the order, by the exact change of v's two gains when u moves
-// from C[u] to D[u]; v survives iff the adjusted delta is >= 0.
+// precedes v in the order; v survives iff the adjusted delta is >= 0.
 template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     k_afterburner(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
+  constexpr int U = GS == 1 ? 8 : 4;
   __shared__ long long rs[GS > 32 ? GS / 32 : 1];
   long long cntM = 0;
   const int r = Grp<GS>::rank();
   for_each_vertex<GS>(count, [&](int64_t i, bool active) {
     const int32_t v = active ? list[i] : 0;
     const int32_t Dv = active ? a.D[v] : kNone;
-    const bool cand = Dv != kNone;
     long long acc = 0;
-    if (cand) {
-      const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
-      const int32_t Cv = a.C[v];
-      const long long qv = a.q[v], wv = a.g.vw[v];
-      const uint32_t hv = fmix32((uint32_t)v ^ a.m.seed);
-      for (int64_t e = beg + r; e < end; e += GS) {
-        const int32_t u = __ldg(a.g.col + e);
-        const int32_t Du = a.D[u];
-        if (Du == kNone) continue;
-        const long long qu = a.q[u];
-        if (!earlier(qu, fmix32((uint32_t)u ^ a.m.seed), u, qv, hv, v)) continue;
-        const int32_t Cu = a.C[u];
-        const long long aw = a.m.Lam * (long long)__ldg(a.g.ew + e) - a.m.mu * a.g.vw[u] * wv;
-        if (Cv == Cu)
-          acc += aw;
-        else if (Dv == Cu)
-          acc -= aw;
-        if (Cv == Du)
-          acc -= aw;
-        else if (Dv >= 0 && Dv == Du)
-          acc += aw;
-      }
+    if (Dv != kNone) {
+      const AbCtx c = ab_ctx(a, v);
+      acc = ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r);
     }
-    if constexpr (GS <= 32) {
-      acc = group_sum<GS>(acc);
-    } else {
-      acc = Grp<GS>::sum(acc, rs);
-    }
+    acc = Grp<GS>::sum(acc, rs);
     if (active && r == 0) {
-      const bool keep = cand && a.delta[v] + acc >= 0;
+      const bool keep = Dv != kNone && a.delta[v] + acc >= 0;
       a.M[v] = keep;
       cntM += keep;
     }
   });
+  flush_block_sum(cntM, &a.sc->count_M);
+}
+
+__global__ void __launch_bounds__(kHubThreads) k_hub_afterburner(PassArgs a) {
+  const int c = blockIdx.x;
+  const int h = a.hub.hub_of[c];
+  const int32_t v = a.hub.vtx[h];
+  if (a.D[v] == kNone) return;  // block-uniform
+  const AbCtx ctx = ab_ctx(a, v);
+  const long long acc = ab_edges<kHubThreads, 4>(a, ctx, a.hub.e0[c], a.hub.e1[c], threadIdx.x);
+  hub_acc_add(a, h, acc);
+}
+
+__global__ void k_hub_ab_final(PassArgs a) {
+  long long cntM = 0;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < a.hub.H; h += gridDim.x * blockDim.x) {
+    const int32_t v = a.hub.vtx[h];
+    const long long acc = a.hub.acc[h];
+    a.hub.acc[h] = 0;
+    const bool keep = a.D[v] != kNone && a.delta[v] + acc >= 0;
+    a.M[v] = keep;
+    cntM += keep;
+  }
   flush_block_sum(cntM, &a.sc->count_M);
 }
 
@@ -330,16 +686,35 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     if (active) {
       const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
       Cv = a.C[v];
+#pragma unroll 4
       for (int64_t e = beg + r; e < end; e += GS)
         if (a.C[__ldg(a.g.col + e)] == Cv) self += __ldg(a.g.ew + e);
     }
-    if constexpr (GS <= 32) {
-      self = group_sum<GS>(self);
-    } else {
-      self = Grp<GS>::sum(self, rs);
-    }
+    self = Grp<GS>::sum(self, rs);
     if (active && r == 0) phi += gain_self(a.m, self, a.g.vw[v], a.W[Cv]);
   });
+  flush_block_sum(phi, &a.sc->phi_acc);
+}
+
+__global__ void __launch_bounds__(kHubThreads) k_hub_objective(PassArgs a) {
+  const int c = blockIdx.x;
+  const int h = a.hub.hub_of[c];
+  const int32_t Cv = a.C[a.hub.vtx[h]];
+  long long self = 0;
+#pragma unroll 4
+  for (int64_t e = a.hub.e0[c] + threadIdx.x; e < a.hub.e1[c]; e += kHubThreads)
+    if (a.C[__ldg(a.g.col + e)] == Cv) self += __ldg(a.g.ew + e);
+  hub_acc_add(a, h, self);
+}
+
+__global__ void k_hub_obj_final(PassArgs a) {
+  long long phi = 0;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < a.hub.H; h += gridDim.x * blockDim.x) {
+    const int32_t v = a.hub.vtx[h];
+    const long long self = a.hub.acc[h];
+    a.hub.acc[h] = 0;
+    phi += gain_self(a.m, self, a.g.vw[v], a.W[a.C[v]]);
+  }
   flush_block_sum(phi, &a.sc->phi_acc);
 }
 
@@ -495,6 +870,14 @@ __global__ void k_bin_next_offset(int32_t *offs, int k, const int32_t *total) {
   offs[k + 1] = offs[k] + *total;
 }
 
+__global__ void k_hub_rows(const int64_t *__restrict__ rp, const int32_t *__restrict__ vtx, int H,
+                           int64_t *__restrict__ out) {
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < H; h += gridDim.x * blockDim.x) {
+    out[2 * h] = rp[vtx[h]];
+    out[2 * h + 1] = rp[vtx[h] + 1];
+  }
+}
+
 // ================================================================ host
 
 static inline unsigned blocks_for(int64_t items, int per_block) {
@@ -504,10 +887,18 @@ static inline unsigned blocks_for(int64_t items, int per_block) {
   return (unsigned)b;
 }
 
+// table (8 bytes per slot) + claimed-slot list (2 bytes per half slot)
+static constexpr int block_table_bytes(int slots) { return slots * 8 + slots; }
+
 void configure_kernels() {
-  cudaFuncSetAttribute(k_move_block<kBin3Threads, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kBin3Slots * (int)sizeof(unsigned long long));
+  cudaFuncSetAttribute(k_move_block<64, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(1024));
+  cudaFuncSetAttribute(k_move_block<128, 2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(2048));
+  cudaFuncSetAttribute(k_move_block<256, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(4096));
+  cudaFuncSetAttribute(k_move_block<256, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(8192));
 }
 
 void build_bins(const LevelGraph &g, Bins &b, int32_t *scan_tmp, cudaStream_t s) {
@@ -528,58 +919,118 @@ void finish_bins(Bins &b, const int32_t *h_offs) {
   }
 }
 
+void launch_hub_rows(const int64_t *rp, const int32_t *vtx, int H, int64_t *out, cudaStream_t s) {
+  if (H > 0) k_hub_rows<<<blocks_for(H, 256), 256, 0, s>>>(rp, vtx, H, out);
+}
+
 template <int GS>
-static void launch_vertex_kernel(void (*k)(PassArgs, const int32_t *, int64_t), const PassArgs &a,
-                                 const int32_t *list, int64_t count, cudaStream_t s, size_t smem = 0) {
-  if (count <= 0) return;
+static int launch_vertex_kernel(void (*k)(PassArgs, const int32_t *, int64_t), const PassArgs &a,
+                                BinRange r, cudaStream_t s, size_t smem = 0) {
+  if (r.count <= 0) return 0;
   const int threads = GS > 32 ? GS : 256;
   const int per_block = GS > 32 ? 1 : threads / GS;
-  k<<<blocks_for(count, per_block), threads, smem, s>>>(a, list, count);
+  k<<<blocks_for(r.count, per_block), threads, smem, s>>>(a, r.list, r.count);
+  return 1;
 }
 
-void launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s) {
-  launch_vertex_kernel<8>(k_first_pass<8>, a, b.list[0], b.count[0], s);
-  launch_vertex_kernel<32>(k_first_pass<32>, a, b.list[1], b.count[1], s);
-  launch_vertex_kernel<32>(k_first_pass<32>, a, b.list[2], b.count[2], s);
-  launch_vertex_kernel<kBin3Threads>(k_first_pass<kBin3Threads>, a, b.list[3], b.count[3], s);
-  launch_vertex_kernel<kBin4Threads>(k_first_pass<kBin4Threads>, a, b.list[4], b.count[4], s);
+static inline unsigned hub_final_blocks(int H) { return blocks_for(H, 256); }
+
+// Kernels without tables take runs of bins: bin 0 -> 1 thread, 1 -> 16
+// lanes, 2..4 -> one warp, 5..6 -> 128 threads, 7..8 -> 512 threads.
+int launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  int n = 0;
+  n += launch_vertex_kernel<1>(k_first_pass<1>, a, bin_range(b, 0, 0), s);
+  n += launch_vertex_kernel<16>(k_first_pass<16>, a, bin_range(b, 1, 1), s);
+  n += launch_vertex_kernel<32>(k_first_pass<32>, a, bin_range(b, 2, 4), s);
+  n += launch_vertex_kernel<128>(k_first_pass<128>, a, bin_range(b, 5, 6), s);
+  n += launch_vertex_kernel<512>(k_first_pass<512>, a, bin_range(b, 7, 8), s);
+  if (a.hub.H > 0) {
+    k_hub_first<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    k_hub_decide<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a, 1);
+    n += 2;
+  }
+  return n;
 }
 
-void launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
-  launch_vertex_kernel<8>(k_move_small<8>, a, b.list[0], b.count[0], s);
-  launch_vertex_kernel<32>(k_move_small<32>, a, b.list[1], b.count[1], s);
-  if (b.count[2] > 0)
-    k_move_warp<<<blocks_for(b.count[2], kBin2Warps), kBin2Warps * 32, 0, s>>>(a, b.list[2],
-                                                                              b.count[2]);
-  launch_vertex_kernel<kBin3Threads>(k_move_block<kBin3Threads, true>, a, b.list[3], b.count[3], s,
-                                     kBin3Slots * sizeof(unsigned long long));
-  launch_vertex_kernel<kBin4Threads>(k_move_block<kBin4Threads, false>, a, b.list[4], b.count[4], s);
+template <int GS, int SLOTS>
+static int launch_move_block(const PassArgs &a, BinRange r, cudaStream_t s) {
+  if (r.count <= 0) return 0;
+  k_move_block<GS, SLOTS><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.list, r.count);
+  return 1;
 }
 
-void launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s) {
-  launch_vertex_kernel<8>(k_afterburner<8>, a, b.list[0], b.count[0], s);
-  launch_vertex_kernel<32>(k_afterburner<32>, a, b.list[1], b.count[1], s);
-  launch_vertex_kernel<32>(k_afterburner<32>, a, b.list[2], b.count[2], s);
-  launch_vertex_kernel<kBin3Threads>(k_afterburner<kBin3Threads>, a, b.list[3], b.count[3], s);
-  launch_vertex_kernel<kBin4Threads>(k_afterburner<kBin4Threads>, a, b.list[4], b.count[4], s);
+template <int SLOTS>
+static int launch_move_warp(const PassArgs &a, BinRange r, cudaStream_t s) {
+  if (r.count <= 0) return 0;
+  k_move_warp<SLOTS><<<blocks_for(r.count, kWarpBinWarps), kWarpBinWarps * 32, 0, s>>>(a, r.list, r.count);
+  return 1;
 }
 
-void launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
-  launch_vertex_kernel<8>(k_objective<8>, a, b.list[0], b.count[0], s);
-  launch_vertex_kernel<32>(k_objective<32>, a, b.list[1], b.count[1], s);
-  launch_vertex_kernel<32>(k_objective<32>, a, b.list[2], b.count[2], s);
-  launch_vertex_kernel<kBin3Threads>(k_objective<kBin3Threads>, a, b.list[3], b.count[3], s);
-  launch_vertex_kernel<kBin4Threads>(k_objective<kBin4Threads>, a, b.list[4], b.count[4], s);
+int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  int n = 0;
+  const BinRange r0 = bin_range(b, 0, 0);
+  if (r0.count > 0) {
+    k_move_thread<<<blocks_for(r0.count, 256), 256, 0, s>>>(a, r0.list, r0.count);
+    n++;
+  }
+  n += launch_vertex_kernel<16>(k_move_small<16>, a, bin_range(b, 1, 1), s);
+  n += launch_vertex_kernel<32>(k_move_small<32>, a, bin_range(b, 2, 2), s);
+  n += launch_move_warp<256>(a, bin_range(b, 3, 3), s);
+  n += launch_move_warp<512>(a, bin_range(b, 4, 4), s);
+  n += launch_move_block<64, 1024>(a, bin_range(b, 5, 5), s);
+  n += launch_move_block<128, 2048>(a, bin_range(b, 6, 6), s);
+  n += launch_move_block<256, 4096>(a, bin_range(b, 7, 7), s);
+  n += launch_move_block<256, 8192>(a, bin_range(b, 8, 8), s);
+  if (a.hub.H > 0) {
+    k_hub_move_insert<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    k_hub_move_scan<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    k_hub_decide<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a, 0);
+    n += 3;
+  }
+  return n;
 }
 
-void launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist,
-                  int32_t *scan_tmp, cudaStream_t s) {
+int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  int n = 1;
+  k_ab_prep<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
+  n += launch_vertex_kernel<1>(k_afterburner<1>, a, bin_range(b, 0, 0), s);
+  n += launch_vertex_kernel<16>(k_afterburner<16>, a, bin_range(b, 1, 1), s);
+  n += launch_vertex_kernel<32>(k_afterburner<32>, a, bin_range(b, 2, 4), s);
+  n += launch_vertex_kernel<128>(k_afterburner<128>, a, bin_range(b, 5, 6), s);
+  n += launch_vertex_kernel<512>(k_afterburner<512>, a, bin_range(b, 7, 8), s);
+  if (a.hub.H > 0) {
+    k_hub_afterburner<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    k_hub_ab_final<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a);
+    n += 2;
+  }
+  return n;
+}
+
+int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  int n = 0;
+  n += launch_vertex_kernel<1>(k_objective<1>, a, bin_range(b, 0, 0), s);
+  n += launch_vertex_kernel<16>(k_objective<16>, a, bin_range(b, 1, 1), s);
+  n += launch_vertex_kernel<32>(k_objective<32>, a, bin_range(b, 2, 4), s);
+  n += launch_vertex_kernel<128>(k_objective<128>, a, bin_range(b, 5, 6), s);
+  n += launch_vertex_kernel<512>(k_objective<512>, a, bin_range(b, 7, 8), s);
+  if (a.hub.H > 0) {
+    k_hub_objective<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    k_hub_obj_final<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a);
+    n += 2;
+  }
+  return n;
+}
+
+int launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist, int32_t *scan_tmp,
+                 cudaStream_t s) {
   k_apply<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, E);
   const int *k = &a.sc->empty_movers;
   k_zero_if<<<blocks_for(a.g.n, 256), 256, 0, s>>>(used, a.g.n, k);
   k_mark_occupied<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a.C, E, used, a.g.n, k);
   scan_apply<int32_t>(a.g.n, FreeFlag{used}, FreeEmit{freelist, k}, scan_tmp, s, k);
-  scan_apply<int32_t>(a.g.n, MoverFlag{E}, MoverEmit{freelist, a.C, a.W, a.g.vw, a.g.n, &a.sc->error}, scan_tmp, s, k);
+  scan_apply<int32_t>(a.g.n, MoverFlag{E}, MoverEmit{freelist, a.C, a.W, a.g.vw, a.g.n, &a.sc->error},
+                      scan_tmp, s, k);
+  return 9;
 }
 
 void launch_pass_begin(Scalars *sc, cudaStream_t s) { k_pass_begin<<<1, 1, 0, s>>>(sc); }

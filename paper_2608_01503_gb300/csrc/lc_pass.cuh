@@ -13,12 +13,12 @@ struct PassArgs {
   int64_t *W;       // W(X) for X in [0, n)
   int32_t *D;       // destination of candidates; kNone for non-candidates
   int64_t *delta;   // g(v, D[v]) - g(v, C[v]) of candidates
-  int64_t *q;       // epsilon bucket of delta (ordering of Section IV-A-1)
+  AbRec *ab;        // per-pass {C, D, epsilon bucket of delta} (Section IV-A-1 order)
   uint8_t *M;       // afterburner survivors
   Scalars *sc;
   unsigned long long *gtab;  // clean global hash scratch, >= 2 nnz slots
   int32_t phi_n, phi_d;      // temperature of this pass
-  int32_t decide;            // 0: accumulate the objective only
+  Hubs hub;                  // chunk plan of the hub bin of this level
 };
 
 // Vertex lists of the degree bins of one level (stable: ascending ids).
@@ -29,21 +29,34 @@ struct Bins {
   int64_t count[kBins];
 };
 
+// Bins are stored one after the other, so a run of bins is one list.
+struct BinRange {
+  const int32_t *list;
+  int64_t count;
+};
+inline BinRange bin_range(const Bins &b, int lo, int hi) {
+  BinRange r{b.list[lo], 0};
+  for (int k = lo; k <= hi; ++k) r.count += b.count[k];
+  return r;
+}
+
 void configure_kernels();
 // Builds b.lists / b.offs on the stream; the caller copies b.offs to the host
 // and fills b.list / b.count (see finish_bins).
 void build_bins(const LevelGraph &g, Bins &b, int32_t *scan_tmp, cudaStream_t s);
 void finish_bins(Bins &b, const int32_t *h_offs);
 
+// Launchers return the number of kernels they launched.
+void launch_hub_rows(const int64_t *rp, const int32_t *vtx, int H, int64_t *out, cudaStream_t s);
 void launch_pass_begin(Scalars *sc, cudaStream_t s);
-void launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
-void launch_move(const PassArgs &a, const Bins &b, cudaStream_t s);
-void launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
-void launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
+int launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
+int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s);
+int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
+int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
 // Update step: moves, W, then ids for movers to new empty clusters.
 // E: uint8[n], used: int32[n], freelist: int32[n] scratch.
-void launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist,
-                  int32_t *scan_tmp, cudaStream_t s);
+int launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist,
+                 int32_t *scan_tmp, cudaStream_t s);
 void launch_bestof(Scalars *sc, const int32_t *C, int32_t *C_out, int64_t n, cudaStream_t s);
 void launch_iota(int32_t *C, int64_t n, cudaStream_t s);
 void launch_cluster_weights(const int32_t *C, const int64_t *vw, int64_t *W, int64_t n,

@@ -201,7 +201,33 @@ def test_sbm_planted_10k_bitexact():
     assert res["modularity"] > 0.48
 
 
-@pytest.mark.parametrize("scale", [12, 15])
+def degree_classes_graph(seed=0, lam=None):
+    """Centres with degrees in every bin (20 .. 6000) over shared leaves, plus
+    random leaf-leaf edges, so every kernel variant and the hub path run."""
+    rng = np.random.default_rng(seed)
+    n_leaves = 7000
+    centres = [20, 100, 200, 400, 800, 1600, 3000, 6000]
+    n = n_leaves + len(centres)
+    src, dst = [], []
+    for i, d in enumerate(centres):
+        leaves = rng.choice(n_leaves, size=d, replace=False)
+        src += [n_leaves + i] * d
+        dst += leaves.tolist()
+    extra = rng.integers(0, n_leaves, size=(20000, 2))
+    src += extra[:, 0].tolist()
+    dst += extra[:, 1].tolist()
+    rp, col, ew = gg.from_edges(n, src, dst, seed=seed, wmin=1, wmax=6)
+    if lam is None:
+        return gg.modularity_inputs(rp, col, ew)
+    return gg.cpm_inputs(rp, col, ew, *lam)
+
+
+def test_every_degree_bin():
+    check_full(degree_classes_graph(0), trace=True)
+    check_full(degree_classes_graph(1, lam=(1, 40)), trace=False)
+
+
+@pytest.mark.parametrize("scale", [12, 15, 16])
 def test_rmat_bitexact(scale):
     """R-MAT with the Graph500 quadrants, weights in [1, 8], modularity.
     Scale 15 has hubs above 4096 (global-table bin) and many isolated vertices."""

@@ -199,6 +199,34 @@ LC_API int lc_objective(const lc_csr *g, const int64_t *vertex_w, const int32_t 
                  int64_t lambda_num, int64_t lambda_den, const int32_t *labels,
                  const lc_opts *opts, lc_result *res);
 
+/* Allocation-free variant of lc_objective.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need the objective (an application whose memory pool already
+ * holds the whole GPU, or a latency-bound service that forbids
+ * cudaMalloc/cudaFree after start-up because they can synchronise the
+ * device).  It computes res->phi, res->objective, res->modularity and
+ * res->n_clusters exactly as lc_objective does, with the same argument
+ * layout (device pointers, caller-owned), and calls no cudaMalloc,
+ * cudaFree or allocating routine.  Its scratch is one fixed array compiled
+ * into liblc (about 36 MiB: 8 bytes plus 1 byte per vertex for
+ * lc_objective_static_max_vertices() = 4,194,304 vertices, and a few
+ * counters), held by every GPU on which the library is loaded until the
+ * process exits.  A graph with more vertices is rejected with LC_ERR_ARG
+ * and res->error_detail set to that maximum.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Every call shares the array and
+ * clears the parts that must start at zero; calls whose work overlaps on
+ * the GPU (e.g. issued on different streams without ordering) race on it.
+ * The CSR preconditions are not validated; labels outside [0, n) give
+ * LC_ERR_ARG; inputs beyond the exactness guards give LC_ERR_OVERFLOW.
+ * Work is issued on opts->stream (opts may be NULL) and the call returns
+ * after the result is on the host. */
+LC_API int lc_objective_static(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                               int64_t lambda_num, int64_t lambda_den, const int32_t *labels,
+                               const lc_opts *opts, lc_result *res);
+/* Largest vertex count lc_objective_static accepts. */
+LC_API int64_t lc_objective_static_max_vertices(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ Functions carry the C names:
   lc_local_move     one LocalMovePasses call (Algorithm 2 + Algorithm 3)
   lc_contract       graph contraction (Algorithm 4)
   lc_objective      exact LambdaCC objective (Eq. 1)
+  lc_objective_static  the same without allocating device memory
   lc_strerror       name of an error code
 """
 from __future__ import annotations
@@ -74,7 +75,7 @@ class _Result(ctypes.Structure):
 
 
 EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_host", "lc_local_move",
-           "lc_contract", "lc_objective"]
+           "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices"]
 
 
 def library_path() -> str:
@@ -104,7 +105,11 @@ def load(build_if_missing: bool = True):
     lib.lc_local_move.argtypes = [csr, P, P, i64, i64, opts, P, i32, res]
     lib.lc_contract.argtypes = [csr, P, P, P, i64, opts, P, P, P, P, i64, ctypes.POINTER(i64)]
     lib.lc_objective.argtypes = [csr, P, P, i64, i64, P, opts, res]
-    for f in ("lc_cluster", "lc_cluster_host", "lc_local_move", "lc_contract", "lc_objective"):
+    lib.lc_objective_static.argtypes = [csr, P, P, i64, i64, P, opts, res]
+    lib.lc_objective_static_max_vertices.argtypes = []
+    lib.lc_objective_static_max_vertices.restype = ctypes.c_int64
+    for f in ("lc_cluster", "lc_cluster_host", "lc_local_move", "lc_contract", "lc_objective",
+              "lc_objective_static"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -307,5 +312,30 @@ def lc_objective(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, labels,
     rc = lib.lc_objective(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
                           int(lambda_num), int(lambda_den), _dev(labels, torch.int32, "labels"),
                           ctypes.byref(c), ctypes.byref(res))
+    _check(rc, res)
+    return _result(res)
+
+
+def lc_objective_static_max_vertices() -> int:
+    return int(load().lc_objective_static_max_vertices())
+
+
+def lc_objective_static(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, labels,
+                        stream=None) -> dict:
+    """lc_objective without any device allocation (for callers that cannot
+    allocate at that point: a pool that owns the whole GPU, or a service
+    that forbids cudaMalloc after start-up).  Scratch is a fixed array in
+    the library; graphs above lc_objective_static_max_vertices() vertices
+    are rejected.  Calls overlapping on the GPU race on that array."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    c = _c_opts(None, _stream_handle(stream))
+    res = _Result()
+    rc = lib.lc_objective_static(ctypes.byref(csr), _dev(vw, torch.int64, "vw"),
+                                 _dev(ew, torch.int32, "ew"), int(lambda_num), int(lambda_den),
+                                 _dev(labels, torch.int32, "labels"), ctypes.byref(c), ctypes.byref(res))
     _check(rc, res)
     return _result(res)

@@ -251,3 +251,25 @@ def random_labels(n: int, k: int, seed: int) -> np.ndarray:
     """Seeded random clustering of n vertices into at most k labels (int32)."""
     rng = np.random.default_rng(seed)
     return rng.integers(0, max(k, 1), size=n).astype(np.int32)
+
+
+def pack(graphs: list) -> dict:
+    """Packs graphs into one CSR (disjoint union, global vertex ids) for the
+    batched entry point: row_ptr, col, ew, vw, graph_ptr, lam_num, lam_den."""
+    n_off, e_off = [0], [0]
+    for g in graphs:
+        n_off.append(n_off[-1] + g.n)
+        e_off.append(e_off[-1] + g.nnz)
+    rp = np.zeros(n_off[-1] + 1, dtype=np.int64)
+    col = np.empty(e_off[-1], dtype=np.int32)
+    ew = np.empty(e_off[-1], dtype=np.int32)
+    vw = np.empty(n_off[-1], dtype=np.int64)
+    for k, g in enumerate(graphs):
+        rp[n_off[k] + 1:n_off[k + 1] + 1] = g.row_ptr[1:] + e_off[k]
+        col[e_off[k]:e_off[k + 1]] = g.col + n_off[k]
+        ew[e_off[k]:e_off[k + 1]] = g.ew
+        vw[n_off[k]:n_off[k + 1]] = g.vw
+    return {"row_ptr": rp, "col": col, "ew": ew, "vw": vw,
+            "graph_ptr": np.array(n_off, dtype=np.int64),
+            "lam_num": np.array([g.lam_num for g in graphs], dtype=np.int64),
+            "lam_den": np.array([g.lam_den for g in graphs], dtype=np.int64)}

@@ -165,6 +165,24 @@ LC_API const char *lc_strerror(int code);
 LC_API int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
                int64_t lambda_den, const lc_opts *opts, int32_t *labels_out, lc_result *res);
 
+/* Batched Louvain+: `count` independent graphs packed into one CSR g (the
+ * disjoint union, global vertex ids): graph k owns the vertex range
+ * [graph_ptr[k], graph_ptr[k+1]) (graph_ptr: HOST int64[count+1], 0 first,
+ * g->n last) and every edge stays inside its graph (checked with
+ * opts.validate, LC_ERR_ARG otherwise).  Each graph has its own
+ * lambda_num[k] / lambda_den[k] (HOST int64[count]).  All graphs run through
+ * the same kernel launches level by level (a graph that finishes
+ * coarsening drops out of the next levels); each graph's result is exactly
+ * what lc_cluster returns for it alone.  labels_out: device int32[g->n],
+ * labels of graph k numbered 0..k_k-1 within the graph.  res: HOST
+ * lc_result[count], one per graph; the kernel timings of opts.profile and
+ * the edge counters are call-wide and reported in res[0].  The trace
+ * callback is not used by batched calls. */
+LC_API int lc_cluster_batch(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                            int32_t count, const int64_t *graph_ptr, const int64_t *lambda_num,
+                            const int64_t *lambda_den, const lc_opts *opts, int32_t *labels_out,
+                            lc_result *res);
+
 /* Same as lc_cluster with HOST buffers (pinned or pageable): copies the graph
  * to the device on opts->stream, clusters it, and copies labels_out (host
  * int32[n]) back before returning. */

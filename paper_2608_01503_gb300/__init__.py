@@ -7,6 +7,7 @@ is missing or cannot be loaded, every call raises; there is no CPU path.
 
 Functions carry the C names:
   lc_cluster        Louvain+ (Algorithm 1) on device tensors
+  lc_cluster_batch  many graphs packed in one CSR, one launch per step for all
   lc_cluster_host   the same on host (numpy) buffers, copies included
   lc_local_move     one LocalMovePasses call (Algorithm 2 + Algorithm 3)
   lc_contract       graph contraction (Algorithm 4)
@@ -74,7 +75,8 @@ class _Result(ctypes.Structure):
                 ("error_detail", ctypes.c_int64)]
 
 
-EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_host", "lc_local_move",
+EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "lc_cluster_host",
+           "lc_local_move",
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices"]
 
 
@@ -102,14 +104,15 @@ def load(build_if_missing: bool = True):
     lib.lc_strerror.restype = ctypes.c_char_p
     lib.lc_cluster.argtypes = [csr, P, P, i64, i64, opts, P, res]
     lib.lc_cluster_host.argtypes = [csr, P, P, i64, i64, opts, P, res]
+    lib.lc_cluster_batch.argtypes = [csr, P, P, i32, P, P, P, opts, P, res]
     lib.lc_local_move.argtypes = [csr, P, P, i64, i64, opts, P, i32, res]
     lib.lc_contract.argtypes = [csr, P, P, P, i64, opts, P, P, P, P, i64, ctypes.POINTER(i64)]
     lib.lc_objective.argtypes = [csr, P, P, i64, i64, P, opts, res]
     lib.lc_objective_static.argtypes = [csr, P, P, i64, i64, P, opts, res]
     lib.lc_objective_static_max_vertices.argtypes = []
     lib.lc_objective_static_max_vertices.restype = ctypes.c_int64
-    for f in ("lc_cluster", "lc_cluster_host", "lc_local_move", "lc_contract", "lc_objective",
-              "lc_objective_static"):
+    for f in ("lc_cluster", "lc_cluster_batch", "lc_cluster_host", "lc_local_move", "lc_contract",
+              "lc_objective", "lc_objective_static"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -232,6 +235,32 @@ def lc_cluster(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, opts: Opt
                         _dev(labels_out, torch.int32, "labels_out"), ctypes.byref(res))
     _check(rc, res)
     return labels_out, _result(res)
+
+
+def lc_cluster_batch(row_ptr, col, ew, vw, graph_ptr, lambda_num, lambda_den,
+                     opts: Options | None = None, labels_out=None, stream=None):
+    """Batched Louvain+ on a packed CSR (device tensors; graph_ptr, lambda_num
+    and lambda_den are host sequences of length count+1, count, count).
+    Returns (labels int32 CUDA tensor, numbered within each graph; list of
+    per-graph result dicts)."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    gp = np.ascontiguousarray(graph_ptr, dtype=np.int64)
+    ln = np.ascontiguousarray(lambda_num, dtype=np.int64)
+    ld = np.ascontiguousarray(lambda_den, dtype=np.int64)
+    count = int(gp.shape[0] - 1)
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    if labels_out is None:
+        labels_out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+    c = _c_opts(opts, _stream_handle(stream))
+    res = (_Result * max(count, 1))()
+    rc = lib.lc_cluster_batch(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
+                              count, gp.ctypes.data, ln.ctypes.data, ld.ctypes.data, ctypes.byref(c),
+                              _dev(labels_out, torch.int32, "labels_out"), res)
+    _check(rc, res[0])
+    return labels_out, [_result(res[k]) for k in range(count)]
 
 
 def lc_cluster_host(row_ptr: np.ndarray, col: np.ndarray, ew: np.ndarray, vw: np.ndarray,

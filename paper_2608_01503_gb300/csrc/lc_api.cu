@@ -145,33 +145,66 @@ struct Prof {
 
 // ------------------------------------------------------------ the run
 
+// One level G_l of a (packed) batch.  Graph g occupies the vertex range
+// [vbase[g], vbase[g] + nv[g]) of the level; nv[g] = 0 when the graph has
+// already finished coarsening below this level.
 struct Level {
   LevelGraph g{};
   Bins bins{};
   Hubs hub{};
-  int32_t *Cd = nullptr;  // dense coarsening clustering of this level
-  int64_t n_c = 0;
+  int32_t *gid = nullptr;            // [n] graph of each vertex (nullptr: one graph)
+  GraphParam *gp = nullptr;          // [G] device
+  std::vector<int64_t> vbase, nv;    // [G] host
+  std::vector<uint8_t> cont;         // [G] host: graph coarsens further from this level
+  int32_t *Cd = nullptr;             // [n] dense coarse id (-1: graph finished here)
 };
 
 struct Run {
   cudaStream_t s;
   lc_opts o;
   Method m;
-  lc_result *res;
+  lc_result *res;  // [G]
+  int G = 1;
+  std::vector<long long> mu, Lam;
+  std::vector<int> top;  // [G] last level of each graph
   Arena ar;
   Prof prof;
   // scratch sized for G_0
   int32_t *C = nullptr, *D = nullptr, *C_out = nullptr, *freelist = nullptr, *used = nullptr,
-          *newid = nullptr, *cnt = nullptr, *scan32 = nullptr;
-  int64_t *W = nullptr, *delta = nullptr, *bound = nullptr, *off = nullptr,
-          *scan64 = nullptr;
+          *newid = nullptr, *cnt = nullptr, *scan32 = nullptr, *freepos = nullptr, *mrank = nullptr;
+  int64_t *W = nullptr, *delta = nullptr, *bound = nullptr, *off = nullptr, *scan64 = nullptr;
   uint8_t *M = nullptr, *E = nullptr;
   AbRec *ab = nullptr;
   unsigned long long *gtab = nullptr;
-  Scalars *sc = nullptr, *sc_trace = nullptr;
+  long long *gself = nullptr;
+  Scalars *sc = nullptr;
+  // per graph
+  long long *phi_acc = nullptr, *phi_out = nullptr, *phi_trace = nullptr;
+  long long *Tg = nullptr, *Vg = nullptr, *sw2g = nullptr;
+  int *improved = nullptr;
+  int32_t *gstart = nullptr;
+  uint8_t *keep = nullptr;
   GraphStats *st = nullptr;
+  std::vector<long long> hT, hV, hsw2;
   explicit Run(cudaStream_t st_) : s(st_), ar(st_) {}
 };
+
+static int alloc_per_graph(Run &r) {
+  const int G = r.G;
+  LC_TRY(r.ar.get(&r.phi_acc, G));
+  LC_TRY(r.ar.get(&r.phi_out, G));
+  LC_TRY(r.ar.get(&r.phi_trace, G));
+  LC_TRY(r.ar.get(&r.Tg, G));
+  LC_TRY(r.ar.get(&r.Vg, G));
+  LC_TRY(r.ar.get(&r.sw2g, G));
+  LC_TRY(r.ar.get(&r.improved, G));
+  LC_TRY(r.ar.get(&r.gstart, G));
+  LC_TRY(r.ar.get(&r.keep, G));
+  LC_CK(cudaMemsetAsync(r.Tg, 0, 8 * (size_t)G, r.s));
+  LC_CK(cudaMemsetAsync(r.Vg, 0, 8 * (size_t)G, r.s));
+  LC_CK(cudaMemsetAsync(r.sw2g, 0, 8 * (size_t)G, r.s));
+  return LC_OK;
+}
 
 static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.C, n0));
@@ -181,6 +214,8 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.used, n0));
   LC_TRY(r.ar.get(&r.newid, n0));
   LC_TRY(r.ar.get(&r.cnt, n0));
+  LC_TRY(r.ar.get(&r.freepos, n0));
+  LC_TRY(r.ar.get(&r.mrank, n0));
   const int64_t big = 2 * nnz0 > n0 + 1 ? 2 * nnz0 : n0 + 1;
   LC_TRY(r.ar.get(&r.scan32, scan_scratch(big)));
   LC_TRY(r.ar.get(&r.W, n0));
@@ -192,8 +227,8 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.M, n0));
   LC_TRY(r.ar.get(&r.E, n0));
   LC_TRY(r.ar.get(&r.gtab, 2 * nnz0));
+  if (r.G > 1) LC_TRY(r.ar.get(&r.gself, n0));
   LC_TRY(r.ar.get(&r.sc, 1));
-  LC_TRY(r.ar.get(&r.sc_trace, 1));
   LC_CK(cudaMemsetAsync(r.gtab, 0, sizeof(unsigned long long) * (size_t)(2 * nnz0 > 0 ? 2 * nnz0 : 1), r.s));
   LC_CK(cudaMemsetAsync(r.sc, 0, sizeof(Scalars), r.s));
   return LC_OK;
@@ -262,10 +297,33 @@ static int bins_for(Run &r, Level &L) {
   return launch_check();
 }
 
+// Uploads the per-graph constants of a level; active[g] selects the graphs
+// whose vertices may move in the next LocalMovePasses call.
+static int upload_params(Run &r, Level &L, const std::vector<uint8_t> &active) {
+  if (!L.gp) LC_TRY(r.ar.get(&L.gp, r.G));
+  std::vector<GraphParam> h(r.G);
+  for (int g = 0; g < r.G; ++g) {
+    h[g].mu = r.mu[g];
+    h[g].Lam = r.Lam[g];
+    h[g].vbase = (int32_t)L.vbase[g];
+    h[g].active = active[g];
+  }
+  LC_CK(cudaMemcpyAsync(L.gp, h.data(), sizeof(GraphParam) * (size_t)r.G, cudaMemcpyHostToDevice, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  return LC_OK;
+}
+
 static PassArgs pass_args(Run &r, const Level &L) {
   PassArgs a{};
   a.g = L.g;
   a.m = r.m;
+  a.gid = L.gid;
+  a.gp = L.gp;
+  a.G = r.G;
+  a.gself = r.G > 1 ? r.gself : nullptr;
+  a.phi_acc = r.phi_acc;
+  a.phi_out = r.phi_out;
+  a.improved = r.improved;
   a.C = r.C;
   a.W = r.W;
   a.D = r.D;
@@ -278,25 +336,32 @@ static PassArgs pass_args(Run &r, const Level &L) {
   return a;
 }
 
+static int fill_per_graph(Run &r, long long *dst, long long value) {
+  std::vector<long long> h(r.G, value);
+  LC_CK(cudaMemcpyAsync(dst, h.data(), 8 * (size_t)r.G, cudaMemcpyHostToDevice, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  return LC_OK;
+}
 
-// Host copies for the optional trace callback.
+// Host copies for the optional trace callback (single-graph calls only).
 static int emit_pass_event(Run &r, const Level &L, int level, int phase, int pass) {
   const int64_t n = L.g.n;
   PassArgs a = pass_args(r, L);
-  a.sc = r.sc_trace;
-  LC_CK(cudaMemsetAsync(r.sc_trace, 0, sizeof(Scalars), r.s));
+  a.phi_acc = r.phi_trace;
+  LC_CK(cudaMemsetAsync(r.phi_trace, 0, 8 * (size_t)r.G, r.s));
   launch_objective(a, L.bins, r.s);
+  launch_graph_sums(a, r.s);
   LC_TRY(launch_check());
   std::vector<int32_t> C(n > 0 ? n : 1), D(n > 0 ? n : 1);
   std::vector<uint8_t> M(n > 0 ? n : 1);
-  Scalars sct, sc;
+  long long phi = 0;
+  Scalars sc;
   LC_CK(cudaMemcpyAsync(C.data(), r.C, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaMemcpyAsync(D.data(), r.D, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaMemcpyAsync(M.data(), r.M, n, cudaMemcpyDeviceToHost, r.s));
-  LC_CK(cudaMemcpyAsync(&sct, r.sc_trace, sizeof(Scalars), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(&phi, r.phi_trace, 8, cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaMemcpyAsync(&sc, r.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
-  // D of non-survivors is kept (candidates); M marks the afterburner survivors
   lc_event ev;
   memset(&ev, 0, sizeof(ev));
   ev.kind = LC_EV_PASS;
@@ -307,19 +372,22 @@ static int emit_pass_event(Run &r, const Level &L, int level, int phase, int pas
   ev.labels = C.data();
   ev.dest = D.data();
   ev.moved = M.data();
-  ev.phi = sct.phi_acc;
+  ev.phi = phi;
   ev.count_L = sc.count_L;
   ev.count_M = sc.count_M;
   r.o.event_cb(r.o.event_ctx, &ev);
   return LC_OK;
 }
 
-// Algorithm 2: `pass_limit` synchronous passes from r.C; leaves C_out (the
-// best clustering seen, strict improvement) in r.C_out and Phi(C_out) in
-// r.sc->phi_out.
-static int local_move_passes(Run &r, Level &L, bool singleton, int level, int phase) {
+// Algorithm 2: `pass_limit` synchronous passes from r.C for the graphs with
+// active[g]; leaves C_out (the best clustering seen, strict improvement) in
+// r.C_out and Phi(C_out) per graph in r.phi_out.
+static int local_move_passes(Run &r, Level &L, bool singleton, int level, int phase,
+                             const std::vector<uint8_t> &active) {
   const int64_t n = L.g.n, nnz = L.g.nnz;
+  LC_TRY(upload_params(r, L, active));
   PassArgs a = pass_args(r, L);
+  ApplyScratch w{r.E, r.used, r.freelist, r.freepos, r.mrank, r.scan32};
   if (singleton) {
     launch_iota(r.C, n, r.s);
     launch_iota(r.C_out, n, r.s);
@@ -329,10 +397,8 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     launch_cluster_weights(r.C, L.g.vw, r.W, n, r.s);
     r.res->kernel_launches[LC_K_OTHER] += 1;
   }
-  Scalars init{};
-  init.phi_out = singleton ? 0 : LLONG_MIN;  // Phi(singletons) = 0
-  LC_CK(cudaMemcpyAsync(&r.sc->phi_acc, &init.phi_acc, sizeof(long long), cudaMemcpyHostToDevice, r.s));
-  LC_CK(cudaMemcpyAsync(&r.sc->phi_out, &init.phi_out, sizeof(long long), cudaMemcpyHostToDevice, r.s));
+  LC_TRY(fill_per_graph(r, r.phi_out, singleton ? 0 : LLONG_MIN));  // Phi(singletons) = 0
+  LC_CK(cudaMemsetAsync(r.phi_acc, 0, 8 * (size_t)r.G, r.s));
   for (int i = 1; i <= r.o.pass_limit; ++i) {
     a.phi_n = r.o.phi_num[i - 1];
     a.phi_d = r.o.phi_den[i - 1];
@@ -346,31 +412,30 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
       r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
       r.prof.end(12.0 * nnz + 48.0 * n);
       r.prof.begin(LC_K_APPLY);
-      launch_bestof(r.sc, r.C, r.C_out, n, r.s);
+      r.res->kernel_launches[LC_K_APPLY] += launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
       r.prof.end(8.0 * n);
-      r.res->kernel_launches[LC_K_APPLY] += 2;
     }
     r.prof.begin(LC_K_AFTERBURNER);
     r.res->kernel_launches[LC_K_AFTERBURNER] += launch_afterburner(a, L.bins, r.s);
     r.prof.end(5.0 * n);
     r.prof.begin(LC_K_APPLY);
-    r.res->kernel_launches[LC_K_APPLY] += launch_apply(a, r.E, r.used, r.freelist, r.scan32, r.s);
+    r.res->kernel_launches[LC_K_APPLY] += launch_apply(a, w, r.s);
     r.prof.end(14.0 * n);
     LC_TRY(launch_check());
     r.res->passes_total++;
     r.res->edges_local_move += nnz;
-    if (r.o.event_cb) LC_TRY(emit_pass_event(r, L, level, phase, i));
+    if (r.o.event_cb && r.G == 1) LC_TRY(emit_pass_event(r, L, level, phase, i));
   }
   r.prof.begin(LC_K_OBJECTIVE);
-  r.res->kernel_launches[LC_K_OBJECTIVE] += launch_objective(a, L.bins, r.s) + 2;
-  launch_bestof(r.sc, r.C, r.C_out, n, r.s);
+  r.res->kernel_launches[LC_K_OBJECTIVE] +=
+      launch_objective(a, L.bins, r.s) + launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
   r.prof.end(12.0 * nnz + 32.0 * n);
   LC_TRY(launch_check());
-  if (r.o.event_cb) {
+  if (r.o.event_cb && r.G == 1) {
     std::vector<int32_t> C(n > 0 ? n : 1);
     long long phi_out = 0;
     LC_CK(cudaMemcpyAsync(C.data(), r.C_out, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, r.s));
-    LC_CK(cudaMemcpyAsync(&phi_out, &r.sc->phi_out, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(&phi_out, r.phi_out, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
     LC_CK(cudaStreamSynchronize(r.s));
     lc_event ev;
     memset(&ev, 0, sizeof(ev));
@@ -385,26 +450,78 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   return LC_OK;
 }
 
-// Compacts r.C_out into L.Cd; returns n_c through *n_c (host).
-static int compact_level(Run &r, Level &L, int64_t *n_c) {
+// Per-graph number of labels used by C (host nc[G]); also leaves newid
+// (global ascending numbering) and gstart on the device.
+static int count_labels(Run &r, Level &L, const int32_t *C, std::vector<int64_t> &nc, int64_t *total) {
   const int64_t n = L.g.n;
-  LC_TRY(r.ar.get(&L.Cd, n));
-  r.prof.begin(LC_K_CONTRACT);
-  launch_compact_labels(r.C_out, n, r.used, r.newid, L.Cd, r.scan32, r.s);
-  r.prof.end(24.0 * n);
-  r.res->kernel_launches[LC_K_CONTRACT] += 5;
-  int32_t k = 0;
-  LC_CK(cudaMemcpyAsync(&k, compact_total(r.scan32, n), sizeof(int32_t), cudaMemcpyDeviceToHost, r.s));
+  launch_mark_used(C, n, r.used, r.s);
+  launch_number_labels(r.used, n, L.gid, L.gp, nullptr, r.newid, r.gstart, nullptr, r.scan32, r.s);
+  r.res->kernel_launches[LC_K_CONTRACT] += 4;
+  std::vector<int32_t> gs(r.G);
+  int32_t tot = 0;
+  LC_CK(cudaMemcpyAsync(gs.data(), r.gstart, 4 * (size_t)r.G, cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaMemcpyAsync(&tot, compact_total(r.scan32, n), 4, cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
   LC_TRY(launch_check());
-  *n_c = k;
-  L.n_c = k;
+  nc.assign(r.G, 0);
+  int prev = -1;
+  for (int g = 0; g < r.G; ++g) {
+    if (L.nv[g] == 0) continue;
+    if (prev >= 0) nc[prev] = gs[g] - gs[prev];
+    prev = g;
+  }
+  if (prev >= 0) nc[prev] = tot - gs[prev];
+  *total = tot;
   return LC_OK;
 }
 
-// Algorithm 4 on (L.g, L.Cd) into a new level.
+// End of a coarsening level: which graphs continue (|C_l| < |V_l|,
+// Algorithm 1), their dense coarse ids L.Cd and the next level's layout.
+static int compact_level(Run &r, Level &L, Level &N, int level, bool *any) {
+  const int64_t n = L.g.n;
+  std::vector<int64_t> nc;
+  int64_t total = 0;
+  r.prof.begin(LC_K_CONTRACT);
+  LC_TRY(count_labels(r, L, r.C_out, nc, &total));
+  L.cont.assign(r.G, 0);
+  *any = false;
+  for (int g = 0; g < r.G; ++g) {
+    if (L.nv[g] == 0) continue;
+    if (nc[g] < L.nv[g]) {
+      L.cont[g] = 1;
+      *any = true;
+    } else {
+      r.top[g] = level;
+    }
+  }
+  if (!*any) {
+    r.prof.end(24.0 * n);
+    return LC_OK;
+  }
+  N.vbase.assign(r.G, 0);
+  N.nv.assign(r.G, 0);
+  int64_t base = 0;
+  for (int g = 0; g < r.G; ++g) {
+    if (!L.cont[g]) continue;
+    N.vbase[g] = base;
+    N.nv[g] = nc[g];
+    base += nc[g];
+  }
+  N.g.n = base;
+  LC_TRY(r.ar.get(&L.Cd, n));
+  if (r.G > 1) LC_TRY(r.ar.get(&N.gid, N.g.n));
+  LC_CK(cudaMemcpyAsync(r.keep, L.cont.data(), (size_t)r.G, cudaMemcpyHostToDevice, r.s));
+  launch_number_labels(r.used, n, L.gid, L.gp, r.keep, r.newid, r.gstart, N.gid, r.scan32, r.s);
+  launch_relabel(r.C_out, r.newid, L.Cd, n, L.gid, r.gstart, r.keep, 0, r.s);
+  LC_CK(cudaStreamSynchronize(r.s));  // L.cont is read by the copy above
+  r.prof.end(24.0 * n);
+  r.res->kernel_launches[LC_K_CONTRACT] += 4;
+  return launch_check();
+}
+
+// Algorithm 4 on (L.g, L.Cd) into N (whose n, vbase, nv, gid are set).
 static int contract_level(Run &r, Level &L, Level &N, int level) {
-  const int64_t n_c = L.n_c;
+  const int64_t n_c = N.g.n;
   int64_t *rp_c = nullptr, *vw_c = nullptr;
   LC_TRY(r.ar.get(&rp_c, n_c + 1));
   LC_TRY(r.ar.get(&vw_c, n_c));
@@ -427,13 +544,12 @@ static int contract_level(Run &r, Level &L, Level &N, int level) {
   r.res->kernel_launches[LC_K_CONTRACT] += 11 + ni;
   LC_TRY(launch_check());
   r.res->edges_contract += L.g.nnz;
-  N.g.n = n_c;
   N.g.nnz = nnz_c;
   N.g.rp = rp_c;
   N.g.col = col_c;
   N.g.ew = ew_c;
   N.g.vw = vw_c;
-  if (r.o.event_cb) {
+  if (r.o.event_cb && r.G == 1) {
     std::vector<int64_t> h_rp(n_c + 1), h_vw(n_c > 0 ? n_c : 1);
     std::vector<int32_t> h_col(nnz_c > 0 ? nnz_c : 1), h_ew(nnz_c > 0 ? nnz_c : 1),
         h_C(L.g.n > 0 ? L.g.n : 1);
@@ -470,17 +586,19 @@ static int check_opts(const lc_opts &o) {
   return LC_OK;
 }
 
-static int check_graph_args(const lc_csr *g, const int64_t *vw, const int32_t *ew, int64_t mu,
-                            int64_t Lam) {
+static int check_lambda(int64_t mu, int64_t Lam) {
+  return (Lam <= 0 || mu < 0 || mu > Lam) ? LC_ERR_ARG : LC_OK;
+}
+
+static int check_graph_args(const lc_csr *g, const int64_t *vw, const int32_t *ew) {
   if (!g || g->n < 0 || g->n > INT32_MAX || g->nnz < 0) return LC_ERR_ARG;
   if (g->n > 0 && (!g->row_ptr || !vw)) return LC_ERR_ARG;
   if (g->nnz > 0 && (!g->col || !ew)) return LC_ERR_ARG;
-  if (Lam <= 0 || mu < 0 || mu > Lam) return LC_ERR_ARG;
   return LC_OK;
 }
 
-// Statistics, validation and the exactness guards of the header.
-static int prepare(Run &r, const LevelGraph &g, GraphStats *hst) {
+// Statistics, validation and the exactness guards of the header, per graph.
+static int prepare(Run &r, const LevelGraph &g, const int32_t *gid, GraphStats *hst) {
   LC_TRY(r.ar.get(&r.st, 1));
   GraphStats z{};
   z.err_key = ~0ull;
@@ -491,12 +609,25 @@ static int prepare(Run &r, const LevelGraph &g, GraphStats *hst) {
   LC_CK(cudaStreamSynchronize(r.s));
   if (ends[0] != 0 || ends[1] != g.nnz) return LC_ERR_ARG;
   r.prof.begin(LC_K_OTHER);
-  launch_stats(g, r.o.validate, r.st, r.s);
+  launch_stats(g, r.o.validate, r.st, gid, r.Tg, r.Vg, r.sw2g, r.s);
   r.prof.end(16.0 * g.n + 8.0 * g.nnz);
   r.res->kernel_launches[LC_K_OTHER] += g.nnz > 0 ? 2 : 1;
   LC_CK(cudaMemcpyAsync(hst, r.st, sizeof(GraphStats), cudaMemcpyDeviceToHost, r.s));
+  r.hT.assign(r.G, 0);
+  r.hV.assign(r.G, 0);
+  r.hsw2.assign(r.G, 0);
+  if (gid) {
+    LC_CK(cudaMemcpyAsync(r.hT.data(), r.Tg, 8 * (size_t)r.G, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(r.hV.data(), r.Vg, 8 * (size_t)r.G, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaMemcpyAsync(r.hsw2.data(), r.sw2g, 8 * (size_t)r.G, cudaMemcpyDeviceToHost, r.s));
+  }
   LC_CK(cudaStreamSynchronize(r.s));
   LC_TRY(launch_check());
+  if (!gid) {
+    r.hT[0] = hst->T;
+    r.hV[0] = hst->V;
+    r.hsw2[0] = hst->sw2;
+  }
   if (r.o.validate) {
     if (hst->err_key != ~0ull) {
       r.res->error_detail = (int64_t)(hst->err_key & 0xFFFFFFFFFFull);
@@ -504,44 +635,45 @@ static int prepare(Run &r, const LevelGraph &g, GraphStats *hst) {
     }
     if (hst->fp1 != 0 || hst->fp2 != 0) return LC_ERR_ASYMMETRIC;
   }
-  // exactness guards
-  const __int128 T = hst->T, V = hst->V;
-  if (T < 0 || T >= ((__int128)1 << 31)) return LC_ERR_OVERFLOW;
-  if (V < 0 || V >= ((__int128)1 << 62)) return LC_ERR_OVERFLOW;
-  const __int128 B = (__int128)r.m.Lam * T + (__int128)r.m.mu * V * V;
-  if (B >= ((__int128)1 << 60)) return LC_ERR_OVERFLOW;
-  const __int128 qb = (__int128)r.m.eps_den * 2 * B / ((__int128)r.m.eps_num * r.m.Lam);
-  if (qb >= ((__int128)1 << 60)) return LC_ERR_OVERFLOW;
+  // exactness guards, per graph
+  for (int k = 0; k < r.G; ++k) {
+    const __int128 T = r.hT[k], V = r.hV[k];
+    if (T < 0 || T >= ((__int128)1 << 31)) return LC_ERR_OVERFLOW;
+    if (V < 0 || V >= ((__int128)1 << 62)) return LC_ERR_OVERFLOW;
+    const __int128 B = (__int128)r.Lam[k] * T + (__int128)r.mu[k] * V * V;
+    if (B >= ((__int128)1 << 60)) return LC_ERR_OVERFLOW;
+    const __int128 qb = (__int128)r.m.eps_den * 2 * B / ((__int128)r.m.eps_num * r.Lam[k]);
+    if (qb >= ((__int128)1 << 60)) return LC_ERR_OVERFLOW;
+  }
   return LC_OK;
 }
 
-static void fill_method(Run &r, int64_t mu, int64_t Lam) {
-  r.m.mu = mu;
-  r.m.Lam = Lam;
+static void fill_method(Run &r) {
   r.m.eps_num = r.o.eps_num;
   r.m.eps_den = r.o.eps_den;
   r.m.seed = r.o.seed;
 }
 
-static void finish_result(Run &r, lc_result *res, long long phi, const GraphStats &st) {
+static void finish_result(Run &r, int g, lc_result *res, long long phi) {
   res->phi = phi;
-  res->lambda_den = r.m.Lam;
-  res->objective = (double)phi / (double)r.m.Lam;
-  const long long num = phi - (r.m.mu ? r.m.mu * st.sw2 : 0);
-  res->modularity = st.T > 0 ? (double)num / ((double)r.m.Lam * (double)st.T) : 0.0;
+  res->lambda_den = r.Lam[g];
+  res->objective = (double)phi / (double)r.Lam[g];
+  const long long num = phi - (r.mu[g] ? r.mu[g] * r.hsw2[g] : 0);
+  res->modularity = r.hT[g] > 0 ? (double)num / ((double)r.Lam[g] * (double)r.hT[g]) : 0.0;
 }
 
-// Phi(labels) through the objective kernels (labels written to r.C first).
-static int objective_of(Run &r, Level &L, const int32_t *labels, long long *phi) {
+// Phi(labels) per graph through the objective kernels (labels copied to r.C).
+static int objective_of(Run &r, Level &L, const int32_t *labels, std::vector<long long> &phi) {
   const int64_t n = L.g.n;
   LC_CK(cudaMemcpyAsync(r.C, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
   launch_cluster_weights(r.C, L.g.vw, r.W, n, r.s);
   PassArgs a = pass_args(r, L);
-  LC_CK(cudaMemsetAsync(r.sc, 0, sizeof(Scalars), r.s));
+  LC_CK(cudaMemsetAsync(r.phi_acc, 0, 8 * (size_t)r.G, r.s));
   r.prof.begin(LC_K_OBJECTIVE);
-  r.res->kernel_launches[LC_K_OBJECTIVE] += launch_objective(a, L.bins, r.s) + 1;
+  r.res->kernel_launches[LC_K_OBJECTIVE] += launch_objective(a, L.bins, r.s) + launch_graph_sums(a, r.s) + 1;
   r.prof.end(12.0 * L.g.nnz + 32.0 * n);
-  LC_CK(cudaMemcpyAsync(phi, &r.sc->phi_acc, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
+  phi.assign(r.G, 0);
+  LC_CK(cudaMemcpyAsync(phi.data(), r.phi_acc, 8 * (size_t)r.G, cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
   return launch_check();
 }
@@ -553,51 +685,93 @@ static int check_device_error(Run &r) {
   return err ? LC_ERR_DEVICE : LC_OK;
 }
 
-// Algorithm 1.
-static int cluster_impl(Run &r, const LevelGraph &g0, int32_t *labels_out) {
-  lc_result *res = r.res;
+// Level 0 of a call: the caller's graph, graph ids of a packed batch.
+static int level0(Run &r, Level &L, const LevelGraph &g0, const std::vector<int64_t> &gptr) {
+  L.g = g0;
+  L.vbase.assign(r.G, 0);
+  L.nv.assign(r.G, 0);
+  for (int g = 0; g < r.G; ++g) {
+    L.vbase[g] = gptr[g];
+    L.nv[g] = gptr[g + 1] - gptr[g];
+  }
+  if (r.G > 1) {
+    int64_t *d_gptr = nullptr;
+    LC_TRY(r.ar.get(&d_gptr, r.G + 1));
+    LC_TRY(r.ar.get(&L.gid, g0.n));
+    LC_CK(cudaMemcpyAsync(d_gptr, gptr.data(), 8 * (size_t)(r.G + 1), cudaMemcpyHostToDevice, r.s));
+    launch_graph_ids(d_gptr, r.G, L.gid, g0.n, r.s);
+    LC_CK(cudaStreamSynchronize(r.s));
+    r.res->kernel_launches[LC_K_OTHER] += 1;
+  }
+  return LC_OK;
+}
+
+// Algorithm 1 on every graph of the call; labels_out gets each graph's dense
+// ids 0..k-1 (numbered within the graph).
+static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t> &gptr,
+                        int32_t *labels_out) {
   GraphStats st{};
-  LC_TRY(prepare(r, g0, &st));
-  LC_TRY(alloc_scratch(r, g0.n, g0.nnz));
+  LC_TRY(alloc_per_graph(r));
   std::vector<Level> lv(1);
-  lv[0].g = g0;
+  LC_TRY(level0(r, lv[0], g0, gptr));
+  LC_TRY(prepare(r, g0, lv[0].gid, &st));
+  LC_TRY(alloc_scratch(r, g0.n, g0.nnz));
+  r.top.assign(r.G, 0);
   int top = 0;
   for (int l = 0;; ++l) {
     if (l >= kMaxLevels) return LC_ERR_TIMEOUT;
-    LC_TRY(bins_for(r, lv[l]));
-    LC_TRY(local_move_passes(r, lv[l], true, l, 0));
-    int64_t n_c = 0;
-    LC_TRY(compact_level(r, lv[l], &n_c));
-    if (n_c == lv[l].g.n) {
+    Level &L = lv[l];
+    LC_TRY(bins_for(r, L));
+    std::vector<uint8_t> present(r.G);
+    for (int g = 0; g < r.G; ++g) present[g] = L.nv[g] > 0;
+    LC_TRY(local_move_passes(r, L, true, l, 0, present));
+    Level N;
+    bool any = false;
+    LC_TRY(compact_level(r, lv[l], N, l, &any));
+    if (!any) {
       top = l;
       break;
     }
-    lv.emplace_back();
+    lv.push_back(std::move(N));
     LC_TRY(contract_level(r, lv[l], lv[l + 1], l));
   }
-  res->levels = top + 1;
-  // uncoarsening; the top level's C_out is the identity
+  for (int g = 0; g < r.G; ++g) {
+    lc_result &res = r.res[g];
+    res.levels = lv[0].nv[g] > 0 ? r.top[g] + 1 : 0;
+  }
+  // uncoarsening; at the top level every present graph has the singleton
+  // clustering its last local-move call returned
   launch_iota(r.C_out, lv[top].g.n, r.s);
   for (int l = top - 1; l >= 0; --l) {
-    launch_project(lv[l].Cd, r.C_out, r.C, lv[l].g.n, r.s);
-    res->kernel_launches[LC_K_OTHER] += 1;
+    Level &L = lv[l];
+    // the level's parameters were last uploaded by its coarsening call
+    launch_project(L.Cd, r.C_out, r.C, L.g.n, L.gid, L.gp, lv[l + 1].gp, r.s);
+    r.res->kernel_launches[LC_K_OTHER] += 1;
     if (r.o.uncoarsen) {
-      LC_TRY(local_move_passes(r, lv[l], false, l, 1));
+      LC_TRY(local_move_passes(r, L, false, l, 1, L.cont));
     } else {
-      LC_CK(cudaMemcpyAsync(r.C_out, r.C, sizeof(int32_t) * lv[l].g.n, cudaMemcpyDeviceToDevice, r.s));
+      LC_CK(cudaMemcpyAsync(r.C_out, r.C, sizeof(int32_t) * L.g.n, cudaMemcpyDeviceToDevice, r.s));
     }
   }
-  // final dense labels and the exact objective
-  const int64_t n = g0.n;
-  launch_compact_labels(r.C_out, n, r.used, r.newid, labels_out, r.scan32, r.s);
-  res->kernel_launches[LC_K_CONTRACT] += 5;
-  int32_t k = 0;
-  LC_CK(cudaMemcpyAsync(&k, compact_total(r.scan32, n), sizeof(int32_t), cudaMemcpyDeviceToHost, r.s));
-  long long phi = 0;
-  LC_TRY(objective_of(r, lv[0], labels_out, &phi));
-  res->n_clusters = k;
+  // final dense labels per graph and the exact objective per graph
+  Level &L0 = lv[0];
+  std::vector<int64_t> nc;
+  int64_t total = 0;
+  LC_TRY(count_labels(r, L0, r.C_out, nc, &total));
+  launch_relabel(r.C_out, r.newid, labels_out, L0.g.n, L0.gid, r.gstart, nullptr, 1, r.s);
+  std::vector<long long> phi;
+  LC_TRY(objective_of(r, L0, r.C_out, phi));
   LC_TRY(check_device_error(r));
-  finish_result(r, res, phi, st);
+  for (int g = 0; g < r.G; ++g) {
+    lc_result &res = r.res[g];
+    res.n_clusters = nc[g];
+    if (L0.nv[g] > 0) {
+      const int lev = r.top[g] + 1;
+      res.passes_total = r.o.pass_limit * (lev + (r.o.uncoarsen ? lev - 1 : 0));
+    }
+    finish_result(r, g, &res, phi[g]);
+  }
+  if (r.G > 1) r.res[0].passes_total = r.o.pass_limit * (r.top[0] + 1 + (r.o.uncoarsen ? r.top[0] : 0));
   return LC_OK;
 }
 
@@ -607,14 +781,16 @@ static lc_opts resolve_opts(const lc_opts *o) {
   return o ? *o : d;
 }
 
-static int begin_call(Run &r, const lc_opts *opts, lc_result *res) {
+static int begin_call(Run &r, const lc_opts *opts, lc_result *res, int G) {
   r.o = resolve_opts(opts);
   r.res = res;
-  memset(res, 0, sizeof(*res));
+  r.G = G;
+  memset(res, 0, sizeof(lc_result) * (size_t)G);
   LC_TRY(check_opts(r.o));
   keep_pool_memory();
   r.prof.on = r.o.profile != 0;
   r.prof.s = r.s;
+  fill_method(r);
   return LC_OK;
 }
 
@@ -625,9 +801,29 @@ static void end_call(Run &r, int rc) {
   }
   if (rc != LC_OK) {
     int64_t detail = r.res->error_detail;
-    memset(r.res, 0, sizeof(*r.res));
+    memset(r.res, 0, sizeof(lc_result) * (size_t)r.G);
     r.res->error_detail = detail;
   }
+}
+
+// Single-graph set-up shared by the step-level entry points.
+static int single_graph(Run &r, const lc_csr *g, const int64_t *vw, const int32_t *ew, int64_t mu,
+                        int64_t Lam, Level &L, GraphStats *st) {
+  r.mu.assign(1, mu);
+  r.Lam.assign(1, Lam);
+  LC_TRY(alloc_per_graph(r));
+  LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, ew, vw};
+  std::vector<int64_t> gptr{0, g->n};
+  LC_TRY(level0(r, L, g0, gptr));
+  return prepare(r, g0, nullptr, st);
+}
+
+static int labels_in_range(Run &r, const int32_t *labels, int64_t n, int64_t limit) {
+  launch_labels_in_range(labels, n, limit, r.st, r.s);
+  GraphStats st2{};
+  LC_CK(cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  return st2.err_key != ~0ull ? LC_ERR_ARG : LC_OK;
 }
 
 }  // namespace lc
@@ -680,15 +876,45 @@ int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, 
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
   Run r((cudaStream_t)o.stream);
-  int rc = begin_call(r, opts, res);
-  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  int rc = begin_call(r, opts, res, 1);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
+  if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
   if (rc == LC_OK && g->n > 0 && !labels_out) rc = LC_ERR_ARG;
   if (rc == LC_OK && g->n > 0) {
-    fill_method(r, lambda_num, lambda_den);
+    r.mu.assign(1, lambda_num);
+    r.Lam.assign(1, lambda_den);
     LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
-    rc = cluster_impl(r, g0, labels_out);
+    rc = cluster_impl(r, g0, std::vector<int64_t>{0, g->n}, labels_out);
   } else if (rc == LC_OK) {
     res->lambda_den = lambda_den;
+  }
+  end_call(r, rc);
+  return rc;
+}
+
+int lc_cluster_batch(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int32_t count,
+                     const int64_t *graph_ptr, const int64_t *lambda_num, const int64_t *lambda_den,
+                     const lc_opts *opts, int32_t *labels_out, lc_result *res) {
+  if (!res || count < 1 || !graph_ptr || !lambda_num || !lambda_den) return LC_ERR_ARG;
+  lc_opts o = resolve_opts(opts);
+  Run r((cudaStream_t)o.stream);
+  int rc = begin_call(r, opts, res, count);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
+  std::vector<int64_t> gptr(graph_ptr, graph_ptr + count + 1);
+  if (rc == LC_OK) {
+    if (gptr[0] != 0 || gptr[count] != g->n) rc = LC_ERR_ARG;
+    for (int k = 0; rc == LC_OK && k < count; ++k)
+      if (gptr[k + 1] < gptr[k] || check_lambda(lambda_num[k], lambda_den[k]) != LC_OK) rc = LC_ERR_ARG;
+  }
+  if (rc == LC_OK && g->n > 0 && !labels_out) rc = LC_ERR_ARG;
+  if (rc == LC_OK) {
+    r.mu.assign(lambda_num, lambda_num + count);
+    r.Lam.assign(lambda_den, lambda_den + count);
+    for (int k = 0; k < count; ++k) res[k].lambda_den = lambda_den[k];
+    if (g->n > 0) {
+      LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
+      rc = cluster_impl(r, g0, gptr, labels_out);
+    }
   }
   end_call(r, rc);
   return rc;
@@ -698,7 +924,7 @@ int lc_cluster_host(const lc_csr *g, const int64_t *vertex_w, const int32_t *edg
                     int64_t lambda_num, int64_t lambda_den, const lc_opts *opts,
                     int32_t *labels_out, lc_result *res) {
   if (!res) return LC_ERR_ARG;
-  int rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  int rc = check_graph_args(g, vertex_w, edge_w);
   if (rc != LC_OK) return rc;
   if (g->n > 0 && !labels_out) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
@@ -735,48 +961,35 @@ int lc_local_move(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
   Run r((cudaStream_t)o.stream);
-  int rc = begin_call(r, opts, res);
-  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  int rc = begin_call(r, opts, res, 1);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
+  if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
   if (rc == LC_OK && g->n > 0 && !labels_inout) rc = LC_ERR_ARG;
   if (rc == LC_OK && g->n > 0) {
-    fill_method(r, lambda_num, lambda_den);
-    LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
-    GraphStats st{};
-    rc = prepare(r, g0, &st);
-    if (rc == LC_OK) {
-      launch_labels_in_range(labels_inout, g0.n, g0.n, r.st, r.s);
-      GraphStats st2{};
-      if (cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
-          cudaStreamSynchronize(r.s) != cudaSuccess)
-        rc = LC_ERR_CUDA;
-      else if (st2.err_key != ~0ull)
-        rc = LC_ERR_ARG;
-    }
-    if (rc == LC_OK) rc = alloc_scratch(r, g0.n, g0.nnz);
     Level L;
-    L.g = g0;
+    GraphStats st{};
+    rc = single_graph(r, g, vertex_w, edge_w, lambda_num, lambda_den, L, &st);
+    if (rc == LC_OK) rc = labels_in_range(r, labels_inout, g->n, g->n);
+    if (rc == LC_OK) rc = alloc_scratch(r, g->n, g->nnz);
     if (rc == LC_OK) rc = bins_for(r, L);
     if (rc == LC_OK) {
-      cudaMemcpyAsync(r.C, labels_inout, 4 * g0.n, cudaMemcpyDeviceToDevice, r.s);
-      rc = local_move_passes(r, L, singleton_start != 0, 0, singleton_start ? 0 : 1);
+      cudaMemcpyAsync(r.C, labels_inout, 4 * g->n, cudaMemcpyDeviceToDevice, r.s);
+      rc = local_move_passes(r, L, singleton_start != 0, 0, singleton_start ? 0 : 1,
+                             std::vector<uint8_t>{1});
     }
     if (rc == LC_OK) {
-      cudaMemcpyAsync(labels_inout, r.C_out, 4 * g0.n, cudaMemcpyDeviceToDevice, r.s);
+      cudaMemcpyAsync(labels_inout, r.C_out, 4 * g->n, cudaMemcpyDeviceToDevice, r.s);
       long long phi = 0;
-      if (cudaMemcpyAsync(&phi, &r.sc->phi_out, 8, cudaMemcpyDeviceToHost, r.s) != cudaSuccess)
+      std::vector<int64_t> nc;
+      int64_t total = 0;
+      if (cudaMemcpyAsync(&phi, r.phi_out, 8, cudaMemcpyDeviceToHost, r.s) != cudaSuccess)
         rc = LC_ERR_CUDA;
-      int32_t k = 0;
-      if (rc == LC_OK) {
-        launch_compact_labels(labels_inout, g0.n, r.used, r.newid, nullptr, r.scan32, r.s);
-        if (cudaMemcpyAsync(&k, compact_total(r.scan32, g0.n), 4, cudaMemcpyDeviceToHost, r.s) !=
-            cudaSuccess)
-          rc = LC_ERR_CUDA;
-      }
+      if (rc == LC_OK) rc = count_labels(r, L, labels_inout, nc, &total);
       if (rc == LC_OK) rc = check_device_error(r);
       if (rc == LC_OK) {
-        res->n_clusters = k;
+        res->n_clusters = total;
         res->levels = 1;
-        finish_result(r, res, phi, st);
+        finish_result(r, 0, res, phi);
       }
     }
   }
@@ -787,7 +1000,7 @@ int lc_local_move(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_
 int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
                 const int32_t *labels, int64_t n_c, const lc_opts *opts, int64_t *c_row_ptr,
                 int32_t *c_col, int32_t *c_ew, int64_t *c_vw, int64_t cap, int64_t *c_nnz) {
-  int rc = check_graph_args(g, vertex_w, edge_w, 0, 1);
+  int rc = check_graph_args(g, vertex_w, edge_w);
   if (rc != LC_OK) return rc;
   if (n_c < 0 || n_c > g->n || !c_nnz || (g->n > 0 && (!labels || !c_row_ptr || !c_vw)) ||
       cap < 0 || (cap > 0 && (!c_col || !c_ew)))
@@ -796,33 +1009,21 @@ int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
   lc_result tmp;
   lc_opts o = resolve_opts(opts);
   Run r((cudaStream_t)o.stream);
-  rc = begin_call(r, opts, &tmp);
+  rc = begin_call(r, opts, &tmp, 1);
   if (rc != LC_OK) return rc;
   *c_nnz = 0;
   if (g->n == 0) {
     if (c_row_ptr) cudaMemsetAsync(c_row_ptr, 0, 8, r.s);
     return cudaStreamSynchronize(r.s) == cudaSuccess ? LC_OK : LC_ERR_CUDA;
   }
-  fill_method(r, 0, 1);
-  LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
-  GraphStats st{};
-  rc = prepare(r, g0, &st);
-  if (rc == LC_OK) {
-    launch_labels_in_range(labels, g0.n, n_c, r.st, r.s);
-    GraphStats st2{};
-    if (cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
-        cudaStreamSynchronize(r.s) != cudaSuccess)
-      rc = LC_ERR_CUDA;
-    else if (st2.err_key != ~0ull)
-      rc = LC_ERR_ARG;
-  }
-  if (rc == LC_OK) rc = alloc_scratch(r, g0.n, g0.nnz);
   Level L;
-  L.g = g0;
+  GraphStats st{};
+  rc = single_graph(r, g, vertex_w, edge_w, 0, 1, L, &st);
+  if (rc == LC_OK) rc = labels_in_range(r, labels, g->n, n_c);
+  if (rc == LC_OK) rc = alloc_scratch(r, g->n, g->nnz);
   if (rc == LC_OK) rc = bins_for(r, L);
   if (rc == LC_OK) {
     L.Cd = const_cast<int32_t *>(labels);
-    L.n_c = n_c;
     launch_contract_offsets(L.g, L.Cd, n_c, r.bound, r.off, c_vw, r.scan64, r.s);
     launch_contract_insert(L.g, L.Cd, r.off, r.gtab, r.cnt, n_c, &r.sc->error, L.bins.list,
                            L.bins.count, L.hub, r.s);
@@ -836,7 +1037,7 @@ int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
       r.res->error_detail = nnz_c;
     }
     if (rc == LC_OK) {
-      launch_contract_compact(r.gtab, 2 * g0.nnz, c_col, c_ew, r.scan32, r.s);
+      launch_contract_compact(r.gtab, 2 * g->nnz, c_col, c_ew, r.scan32, r.s);
       rc = launch_check();
     }
     if (rc == LC_OK) rc = check_device_error(r);
@@ -852,40 +1053,30 @@ int lc_objective(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
   Run r((cudaStream_t)o.stream);
-  int rc = begin_call(r, opts, res);
-  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w, lambda_num, lambda_den);
+  int rc = begin_call(r, opts, res, 1);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
+  if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
   if (rc == LC_OK && g->n > 0 && !labels) rc = LC_ERR_ARG;
   if (rc == LC_OK && g->n > 0) {
-    fill_method(r, lambda_num, lambda_den);
-    LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
-    GraphStats st{};
-    rc = prepare(r, g0, &st);
-    if (rc == LC_OK) {
-      launch_labels_in_range(labels, g0.n, g0.n, r.st, r.s);
-      GraphStats st2{};
-      if (cudaMemcpyAsync(&st2, r.st, sizeof(st2), cudaMemcpyDeviceToHost, r.s) != cudaSuccess ||
-          cudaStreamSynchronize(r.s) != cudaSuccess)
-        rc = LC_ERR_CUDA;
-      else if (st2.err_key != ~0ull)
-        rc = LC_ERR_ARG;
-    }
-    if (rc == LC_OK) rc = alloc_scratch(r, g0.n, 0);
     Level L;
-    L.g = g0;
+    GraphStats st{};
+    rc = single_graph(r, g, vertex_w, edge_w, lambda_num, lambda_den, L, &st);
+    if (rc == LC_OK) rc = labels_in_range(r, labels, g->n, g->n);
+    if (rc == LC_OK) rc = alloc_scratch(r, g->n, 0);
     if (rc == LC_OK) rc = bins_for(r, L);
-    long long phi = 0;
-    if (rc == LC_OK) rc = objective_of(r, L, labels, &phi);
+    if (rc == LC_OK) rc = upload_params(r, L, std::vector<uint8_t>{1});
+    std::vector<long long> phi;
+    if (rc == LC_OK) rc = objective_of(r, L, labels, phi);
+    std::vector<int64_t> nc;
+    int64_t total = 0;
+    if (rc == LC_OK) rc = count_labels(r, L, labels, nc, &total);
     if (rc == LC_OK) {
-      launch_compact_labels(labels, g0.n, r.used, r.newid, nullptr, r.scan32, r.s);
-      int32_t k = 0;
-      if (cudaMemcpyAsync(&k, compact_total(r.scan32, g0.n), 4, cudaMemcpyDeviceToHost, r.s) !=
-              cudaSuccess ||
-          cudaStreamSynchronize(r.s) != cudaSuccess)
-        rc = LC_ERR_CUDA;
-      res->n_clusters = k;
+      res->n_clusters = total;
       res->levels = 1;
-      finish_result(r, res, phi, st);
+      finish_result(r, 0, res, phi[0]);
     }
+  } else if (rc == LC_OK) {
+    res->lambda_den = lambda_den;
   }
   end_call(r, rc);
   return rc;

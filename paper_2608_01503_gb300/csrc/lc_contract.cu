@@ -25,20 +25,49 @@ __global__ void k_mark_used(const int32_t *__restrict__ C, int32_t *__restrict__
     used[C[v]] = 1;
 }
 
+// Per-graph dense relabelling.  Labels of graph g lie in its vertex range
+// [vbase_g, vbase_g + n_g), so one scan over all labels numbers each graph's
+// labels in order; the prefix at each graph's first vertex gives its start.
 struct UsedIn {
   const int32_t *used;
-  __device__ int32_t operator()(int64_t x) const { return used[x]; }
+  const int32_t *gid;
+  const uint8_t *keep;  // nullable: only labels of graphs with keep[g]
+  __device__ int32_t operator()(int64_t x) const {
+    if (!used[x]) return 0;
+    if (keep && !keep[gid ? gid[x] : 0]) return 0;
+    return 1;
+  }
 };
 struct NewIdOut {
   int32_t *newid;
-  __device__ void operator()(int64_t x, int32_t pos, int32_t) const { newid[x] = pos; }
+  const int32_t *gid;       // nullable (one graph)
+  const GraphParam *gp;     // per-graph vertex bases
+  int32_t *gstart;          // [G]: prefix at each graph's first vertex
+  int32_t *gid_next;        // nullable: graph of each new id
+  __device__ void operator()(int64_t x, int32_t pos, int32_t f) const {
+    newid[x] = pos;
+    const int g = gid ? gid[x] : 0;
+    if (gp[g].vbase == x) gstart[g] = pos;
+    if (f && gid_next) gid_next[pos] = g;
+  }
 };
 
+// out[v] = newid[C[v]] - base, where base is the start of v's graph when
+// `local` is set (labels numbered within each graph); vertices of graphs
+// that do not keep their labels get -1.
 __global__ void k_relabel(const int32_t *__restrict__ C, const int32_t *__restrict__ newid,
-                          int32_t *__restrict__ out, int64_t n) {
+                          int32_t *__restrict__ out, int64_t n, const int32_t *__restrict__ gid,
+                          const int32_t *__restrict__ gstart, const uint8_t *__restrict__ keep,
+                          int local) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    out[v] = newid[C[v]];
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int g = gid ? gid[v] : 0;
+    if (keep && !keep[g]) {
+      out[v] = -1;
+      continue;
+    }
+    out[v] = newid[C[v]] - (local ? gstart[g] : 0);
+  }
 }
 
 // bound[C[v]] += deg(v), vw_c[C[v]] += w(v)
@@ -46,6 +75,7 @@ __global__ void k_bound(LevelGraph g, const int32_t *__restrict__ Cd, int64_t *b
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t x = Cd[v];
+    if (x < 0) continue;  // graph finished coarsening
     const int64_t d = g.rp[v + 1] - g.rp[v];
     if (d) atomicAdd((unsigned long long *)&bound[x], (unsigned long long)d);
     atomicAdd((unsigned long long *)&vw_c[x], (unsigned long long)g.vw[v]);
@@ -114,6 +144,7 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     if (!active) return;
     const int32_t v = list[i];
     const int32_t x = a.Cd[v];
+    if (x < 0) return;  // graph finished coarsening
     bool ok = true;
     const int fresh_n = insert_edges<GS>(a, x, a.g.rp[v], a.g.rp[v + 1], r, ok);
     if (!ok) *a.error = 1;
@@ -126,6 +157,7 @@ __global__ void __launch_bounds__(kHubThreads) k_insert_hub(InsertArgs a, Hubs h
   const int c = blockIdx.x;
   const int32_t v = hub.vtx[hub.hub_of[c]];
   const int32_t x = a.Cd[v];
+  if (x < 0) return;  // graph finished coarsening
   bool ok = true;
   const int fresh_n = insert_edges<kHubThreads>(a, x, hub.e0[c], hub.e1[c], threadIdx.x, ok);
   if (!ok) *a.error = 1;
@@ -155,11 +187,40 @@ struct SlotOut {
   }
 };
 
+// ProjectCluster.  Labels of a graph live in its own vertex range at every
+// level, so a coarse label is rebased from the graph's coarse range to its
+// fine range (one graph: both bases are 0).  A graph that finished
+// coarsening at this level keeps the singleton clustering its last
+// local-move call returned.
 __global__ void k_project(const int32_t *__restrict__ Cd, const int32_t *__restrict__ Cnext,
-                          int32_t *__restrict__ C, int64_t n) {
+                          int32_t *__restrict__ C, int64_t n, const int32_t *__restrict__ gid,
+                          const GraphParam *__restrict__ gp_fine,
+                          const GraphParam *__restrict__ gp_coarse) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    C[v] = Cnext[Cd[v]];
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (Cd[v] < 0) {
+      C[v] = (int32_t)v;
+      continue;
+    }
+    const int g = gid ? gid[v] : 0;
+    C[v] = gp_fine[g].vbase + (Cnext[Cd[v]] - gp_coarse[g].vbase);
+  }
+}
+
+// gid[v] = the graph whose vertex range [gptr[g], gptr[g+1]) holds v.
+__global__ void k_graph_ids(const int64_t *__restrict__ gptr, int G, int32_t *__restrict__ gid, int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = G;  // gptr[lo] <= v < gptr[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (gptr[mid] <= v)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    gid[v] = lo;
+  }
 }
 
 // ================================================================= host
@@ -171,12 +232,20 @@ static inline unsigned blocks_for(int64_t items, int per_block) {
   return (unsigned)b;
 }
 
-void launch_compact_labels(const int32_t *C, int64_t n, int32_t *used, int32_t *newid,
-                           int32_t *Cd, int32_t *scan_tmp, cudaStream_t s) {
+void launch_mark_used(const int32_t *C, int64_t n, int32_t *used, cudaStream_t s) {
   cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s);
   k_mark_used<<<blocks_for(n, 256), 256, 0, s>>>(C, used, n);
-  scan_apply<int32_t>(n, UsedIn{used}, NewIdOut{newid}, scan_tmp, s);
-  if (Cd) k_relabel<<<blocks_for(n, 256), 256, 0, s>>>(C, newid, Cd, n);
+}
+
+void launch_number_labels(const int32_t *used, int64_t n, const int32_t *gid, const GraphParam *gp,
+                          const uint8_t *keep, int32_t *newid, int32_t *gstart, int32_t *gid_next,
+                          int32_t *scan_tmp, cudaStream_t s) {
+  scan_apply<int32_t>(n, UsedIn{used, gid, keep}, NewIdOut{newid, gid, gp, gstart, gid_next}, scan_tmp, s);
+}
+
+void launch_relabel(const int32_t *C, const int32_t *newid, int32_t *out, int64_t n, const int32_t *gid,
+                    const int32_t *gstart, const uint8_t *keep, int local, cudaStream_t s) {
+  k_relabel<<<blocks_for(n, 256), 256, 0, s>>>(C, newid, out, n, gid, gstart, keep, local);
 }
 
 const int32_t *compact_total(const int32_t *scan_tmp, int64_t n) {
@@ -236,8 +305,13 @@ void launch_contract_compact(unsigned long long *tab, int64_t slots, int32_t *co
   scan_apply<int32_t>(slots, SlotIn{tab}, SlotOut{tab, col_c, ew_c}, scan_tmp, s);
 }
 
-void launch_project(const int32_t *Cd, const int32_t *Cnext, int32_t *C, int64_t n, cudaStream_t s) {
-  k_project<<<blocks_for(n, 256), 256, 0, s>>>(Cd, Cnext, C, n);
+void launch_graph_ids(const int64_t *gptr, int G, int32_t *gid, int64_t n, cudaStream_t s) {
+  k_graph_ids<<<blocks_for(n, 256), 256, 0, s>>>(gptr, G, gid, n);
+}
+
+void launch_project(const int32_t *Cd, const int32_t *Cnext, int32_t *C, int64_t n, const int32_t *gid,
+                    const GraphParam *gp_fine, const GraphParam *gp_coarse, cudaStream_t s) {
+  k_project<<<blocks_for(n, 256), 256, 0, s>>>(Cd, Cnext, C, n, gid, gp_fine, gp_coarse);
 }
 
 }  // namespace lc

@@ -66,9 +66,17 @@ struct Hubs {
   int32_t *part_x = nullptr;        // [Q]
 };
 
-// Method constants of one call.
+// Per-graph constants of a (packed) batch: lambda = mu / Lam, the first
+// vertex of the graph in the current level's packed vertex range, and
+// whether the graph runs local-move passes at this level.
+struct GraphParam {
+  long long mu, Lam;
+  int32_t vbase;
+  int32_t active;
+};
+
+// Call-wide constants of the afterburner order (Section IV-A-1).
 struct Method {
-  int64_t mu, Lam;        // lambda = mu / Lam
   int32_t eps_num, eps_den;
   uint32_t seed;
 };
@@ -80,11 +88,8 @@ struct __align__(16) AbRec {
   long long q;
 };
 
-// Device-resident scalars of one LocalMovePasses call.
+// Device-resident counters of one call (all graphs of a batch together).
 struct Scalars {
-  long long phi_acc;     // Phi of the clustering entering the current pass
-  long long phi_out;     // Phi(C_out)
-  int improved;          // phi_acc > phi_out at the last best-of test
   int empty_movers;      // movers to a new empty cluster in this pass
   long long count_L, count_M;
   int error;             // internal bound violation (hash probe overrun)
@@ -117,8 +122,8 @@ __device__ __forceinline__ int32_t slot_val(unsigned long long s) { return (int3
 
 // Insert (key, w) into an open-addressing table of `cap` 64-bit slots with
 // linear probing.  A new key is claimed and its first weight stored in one
-// compare-and-swap; later weights of the key are one atomic add on the low
-// word (values stay below 2^31, so the add never carries into the key).
+// compare-and-swap; later weights of the key are one 32-bit atomic add on
+// the value word (values stay below 2^31, so it never reaches the key).
 // Returns false when all `cap` slots were probed without success, a bound
 // violation (every caller sizes tables to at least twice its distinct keys).
 // When this call claimed a new slot, `fresh` is set and `slot` names it.
@@ -138,7 +143,8 @@ __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap,
       cur = prev;
     }
     if ((cur & 0xFFFFFFFF00000000ull) == tag) {
-      atomicAdd(&tab[s], (unsigned long long)(uint32_t)w);
+      // value word = low 32 bits of the little-endian slot
+      atomicAdd(reinterpret_cast<unsigned int *>(&tab[s]), (unsigned int)w);
       return true;
     }
     s = (s + 1 == cap) ? 0 : s + 1;
@@ -155,14 +161,14 @@ __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap,
 // --------------------------------------------------------------- gains
 
 // Lam-scaled gain of joining cluster X (X != C[v]): Lam*S - mu*w(v)*W(X).
-__device__ __forceinline__ long long gain_other(const Method &m, long long S, long long wv,
+__device__ __forceinline__ long long gain_other(const GraphParam &p, long long S, long long wv,
                                                 long long WX) {
-  return m.Lam * S - m.mu * wv * WX;
+  return p.Lam * S - p.mu * wv * WX;
 }
 // Lam-scaled gain of staying: Lam*S_self - mu*w(v)*(W(C[v]) - w(v)).
-__device__ __forceinline__ long long gain_self(const Method &m, long long S, long long wv,
+__device__ __forceinline__ long long gain_self(const GraphParam &p, long long S, long long wv,
                                                long long WC) {
-  return m.Lam * S - m.mu * wv * (WC - wv);
+  return p.Lam * S - p.mu * wv * (WC - wv);
 }
 
 // Better (gain, id) for the argmax: larger gain, ties to the smaller id.
@@ -172,9 +178,9 @@ __device__ __forceinline__ bool better(long long g1, int32_t x1, long long g2, i
 
 // floor(eps_den * delta / (eps_num * Lam)), the epsilon bucket of the
 // ordering of Section IV-A-1.
-__device__ __forceinline__ long long eps_bucket(const Method &m, long long delta) {
+__device__ __forceinline__ long long eps_bucket(const Method &m, long long Lam, long long delta) {
   __int128 num = (__int128)m.eps_den * delta;
-  __int128 den = (__int128)m.eps_num * m.Lam;
+  __int128 den = (__int128)m.eps_num * Lam;
   __int128 qq = num / den;
   if ((num % den) != 0 && num < 0) qq -= 1;
   return (long long)qq;

@@ -20,14 +20,33 @@
 
 namespace lc {
 
+// ---------------------------------------------------- graphs of a batch
+
+// Graph of vertex v in a packed batch (one graph: 0).
+__device__ __forceinline__ int graph_of(const PassArgs &a, int32_t v) { return a.gid ? a.gid[v] : 0; }
+
+// Records g(v, C[v]) for the objective: one graph accumulates in a register
+// flushed once per block; a batch writes it per vertex and the per-graph
+// sums are formed by k_graph_sums.
+__device__ __forceinline__ void add_self(const PassArgs &a, int32_t v, long long gC, long long &phi) {
+  if (a.gself)
+    a.gself[v] = gC;
+  else
+    phi += gC;
+}
+
 // ---------------------------------------------------- vertex decision
 
 // Algorithm 2 for one vertex once g(v, C[v]) and the best other cluster
 // (gbest, best) are known: the empty-cluster rule, the candidate test with
 // temperature phi = phi_n / phi_d, and delta_v (Algorithm 3's priority; its
 // epsilon bucket is computed by k_ab_prep, off this latency-bound path).
-__device__ __forceinline__ void decide(const PassArgs &a, int32_t v, long long gC, int32_t best,
-                                       long long gbest, long long &cntL) {
+__device__ __forceinline__ void decide(const PassArgs &a, const GraphParam &P, int32_t v, long long gC,
+                                       int32_t best, long long gbest, long long &cntL) {
+  if (!P.active) {  // graph not moving at this level (finished coarsening earlier)
+    a.D[v] = kNone;
+    return;
+  }
   if (gC < 0 && (best == kNone || gbest < 0)) {
     best = kEmpty;
     gbest = 0;
@@ -48,10 +67,10 @@ __device__ __forceinline__ void decide(const PassArgs &a, int32_t v, long long g
 // Singleton start: the adjacent clusters of v are its neighbours, so the
 // gains are read straight from the CSR: g(v,{u}) = Lam*w(u,v) - mu*w(v)*w(u),
 // and g(v, C[v]) = 0.
-__device__ __forceinline__ void first_edge(const PassArgs &a, int64_t e, long long wv, long long &gb,
-                                           int32_t &xb) {
+__device__ __forceinline__ void first_edge(const PassArgs &a, const GraphParam &P, int64_t e,
+                                           long long wv, long long &gb, int32_t &xb) {
   const int32_t u = __ldg(a.g.col + e);
-  const long long g = a.m.Lam * (long long)__ldg(a.g.ew + e) - a.m.mu * wv * __ldg(a.g.vw + u);
+  const long long g = P.Lam * (long long)__ldg(a.g.ew + e) - P.mu * wv * __ldg(a.g.vw + u);
   if (better(g, u, gb, xb)) {
     gb = g;
     xb = u;
@@ -69,12 +88,13 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     const int32_t v = active ? list[i] : 0;
     const int64_t beg = active ? a.g.rp[v] : 0, end = active ? a.g.rp[v + 1] : 0;
     const long long wv = active ? a.g.vw[v] : 0;
+    const GraphParam P = a.gp[graph_of(a, v)];
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
 #pragma unroll 4
-    for (int64_t e = beg + r; e < end; e += GS) first_edge(a, e, wv, gb, xb);
+    for (int64_t e = beg + r; e < end; e += GS) first_edge(a, P, e, wv, gb, xb);
     Grp<GS>::argmax(gb, xb, rg, rx);
-    if (active && r == 0) decide(a, v, 0, xb, gb, cntL);
+    if (active && r == 0) decide(a, P, v, 0, xb, gb, cntL);
   });
   flush_block_sum(cntL, &a.sc->count_L);
 }
@@ -83,8 +103,8 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
 
 // One thread per vertex of degree <= 8: neighbour clusters and weights are
 // held in registers; S(v, X) for each distinct X is an unrolled compare-sum.
-__global__ void __launch_bounds__(256) k_move_thread(PassArgs a, const int32_t *__restrict__ list,
-                                                     int64_t count) {
+__global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const int32_t *__restrict__ list,
+                                                        int64_t count) {
   constexpr int K = 8;
   long long cntL = 0, phi = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -94,6 +114,7 @@ __global__ void __launch_bounds__(256) k_move_thread(PassArgs a, const int32_t *
     const int deg = (int)(a.g.rp[v + 1] - beg);
     const int32_t Cv = a.C[v];
     const long long wv = a.g.vw[v];
+    const GraphParam P = a.gp[graph_of(a, v)];
     int32_t u[K], w[K], X[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -129,19 +150,19 @@ __global__ void __launch_bounds__(256) k_move_thread(PassArgs a, const int32_t *
         }
       }
       if (first) {
-        const long long g = gain_other(a.m, S, wv, WX[j]);
+        const long long g = gain_other(P, S, wv, WX[j]);
         if (better(g, X[j], gb, xb)) {
           gb = g;
           xb = X[j];
         }
       }
     }
-    const long long gC = gain_self(a.m, self, wv, WC);
-    phi += gC;
-    decide(a, v, gC, xb, gb, cntL);
+    const long long gC = gain_self(P, self, wv, WC);
+    add_self(a, v, gC, phi);
+    decide(a, P, v, gC, xb, gb, cntL);
   }
   flush_block_sum(cntL, &a.sc->count_L);
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 // ------------------------------------ aggregation + argmax, bins 1-2 (lanes)
@@ -163,6 +184,7 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
     const int64_t beg = active ? a.g.rp[v] : 0, deg = active ? a.g.rp[v + 1] - beg : 0;
     const int32_t Cv = active ? a.C[v] : 0;
     const long long wv = active ? a.g.vw[v] : 0;
+    const GraphParam P = a.gp[graph_of(a, v)];
     const bool has = sub < deg;
     int32_t X = -1, w = 0;
     if (has) {
@@ -186,19 +208,19 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
     long long g = LLONG_MIN;
     int32_t x = kNone;
     if (other && lane == leader) {
-      g = gain_other(a.m, acc[threadIdx.x], wv, WX);
+      g = gain_other(P, acc[threadIdx.x], wv, WX);
       x = X;
     }
     group_argmax<G>(g, x);
     if (active && sub == 0) {
-      const long long gC = gain_self(a.m, S_self, wv, WC);
-      phi += gC;
-      decide(a, v, gC, x, g, cntL);
+      const long long gC = gain_self(P, S_self, wv, WC);
+      add_self(a, v, gC, phi);
+      decide(a, P, v, gC, x, g, cntL);
     }
     __syncwarp();
   });
   flush_block_sum(cntL, &a.sc->count_L);
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 // ------------------------------------ shared-table aggregation, bins 3-5
@@ -212,13 +234,14 @@ __device__ __forceinline__ uint32_t table_cap(int64_t deg) {
 }
 
 // Inserts edges [beg, end) of v (strided by GS, loads batched U at a time)
-// into `tab`; claimed slots are appended to `list` (counter `nlist`).
-// Returns this thread's part of S(v, C[v]).
+// into `tab`; claimed slots are appended to `list` (counter `nlist`, appends
+// warp-aggregated).  Returns this thread's part of S(v, C[v]).
 template <int GS, int U>
 __device__ __forceinline__ long long table_insert_row(const PassArgs &a, int64_t beg, int64_t end,
                                                       int32_t Cv, unsigned long long *tab,
                                                       uint32_t cap, uint16_t *list, int *nlist,
                                                       int r, bool &ok) {
+  const int lane = threadIdx.x & 31;
   long long self = 0;
   for (int64_t base = beg; base < end; base += GS * U) {
     int32_t u[U], w[U], X[U];
@@ -236,14 +259,20 @@ __device__ __forceinline__ long long table_insert_row(const PassArgs &a, int64_t
     for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-      if (u[k] < 0) continue;
-      if (X[k] == Cv) {
-        self += w[k];
-      } else {
-        bool fresh = false;
-        uint32_t slot = 0;
-        ok &= table_add(tab, cap, X[k], w[k], fresh, slot);
-        if (fresh) list[atomicAdd(nlist, 1)] = (uint16_t)slot;
+      bool fresh = false;
+      uint32_t slot = 0;
+      if (u[k] >= 0) {
+        if (X[k] == Cv)
+          self += w[k];
+        else
+          ok &= table_add(tab, cap, X[k], w[k], fresh, slot);
+      }
+      const unsigned fm = __ballot_sync(0xFFFFFFFFu, fresh);
+      if (fm) {
+        int basepos = 0;
+        if (lane == __ffs(fm) - 1) basepos = atomicAdd(nlist, __popc(fm));
+        basepos = __shfl_sync(0xFFFFFFFFu, basepos, __ffs(fm) - 1);
+        if (fresh) list[basepos + __popc(fm & ((1u << lane) - 1))] = (uint16_t)slot;
       }
     }
   }
@@ -253,9 +282,9 @@ __device__ __forceinline__ long long table_insert_row(const PassArgs &a, int64_t
 // Best (gain, cluster) over the claimed slots list[0 .. n) (strided by GS);
 // resets every slot it reads.
 template <int GS>
-__device__ __forceinline__ void list_argmax(const PassArgs &a, unsigned long long *tab,
-                                            const uint16_t *list, int n, long long wv, int r,
-                                            long long &gb, int32_t &xb) {
+__device__ __forceinline__ void list_argmax(const PassArgs &a, const GraphParam &P,
+                                            unsigned long long *tab, const uint16_t *list, int n,
+                                            long long wv, int r, long long &gb, int32_t &xb) {
   constexpr int U = 4;
   for (int base = 0; base < n; base += GS * U) {
     unsigned long long t[U];
@@ -276,7 +305,7 @@ __device__ __forceinline__ void list_argmax(const PassArgs &a, unsigned long lon
     for (int k = 0; k < U; ++k) {
       if (t[k] == kEmptySlot) continue;
       const int32_t X = slot_key(t[k]);
-      const long long g = gain_other(a.m, slot_val(t[k]), wv, WX[k]);
+      const long long g = gain_other(P, slot_val(t[k]), wv, WX[k]);
       if (better(g, X, gb, xb)) {
         gb = g;
         xb = X;
@@ -288,9 +317,9 @@ __device__ __forceinline__ void list_argmax(const PassArgs &a, unsigned long lon
 // Best (gain, cluster) over slots [s0, s1) of a global table (strided by
 // GS), resetting the slots it reads (hub chunks).
 template <int GS>
-__device__ __forceinline__ void range_argmax(const PassArgs &a, unsigned long long *tab, uint32_t s0,
-                                             uint32_t s1, long long wv, int r, long long &gb,
-                                             int32_t &xb) {
+__device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam &P,
+                                             unsigned long long *tab, uint32_t s0, uint32_t s1,
+                                             long long wv, int r, long long &gb, int32_t &xb) {
   constexpr int U = 4;
   for (uint32_t base = s0; base < s1; base += GS * U) {
     unsigned long long t[U];
@@ -307,7 +336,7 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, unsigned long lo
     for (int k = 0; k < U; ++k) {
       if (t[k] == kEmptySlot) continue;
       const int32_t X = slot_key(t[k]);
-      const long long g = gain_other(a.m, slot_val(t[k]), wv, WX[k]);
+      const long long g = gain_other(P, slot_val(t[k]), wv, WX[k]);
       if (better(g, X, gb, xb)) {
         gb = g;
         xb = X;
@@ -319,7 +348,7 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, unsigned long lo
 // Bins 3-4: one warp per vertex, a per-warp shared table of SLOTS slots
 // and its claimed-slot list.
 template <int SLOTS>
-__global__ void __launch_bounds__(kWarpBinWarps * 32)
+__global__ void __launch_bounds__(kWarpBinWarps * 32, 5)
     k_move_warp(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
   constexpr int U = SLOTS / 64;  // one batch of loads covers the largest row of the bin
   __shared__ unsigned long long tabs[kWarpBinWarps][SLOTS];
@@ -337,6 +366,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32)
     const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
     const int32_t Cv = a.C[v];
     const long long wv = a.g.vw[v];
+    const GraphParam P = a.gp[graph_of(a, v)];
     const uint32_t cap = table_cap(end - beg);
     bool ok = true;
     long long self =
@@ -347,19 +377,19 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32)
     const int nl = nlists[wid];
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    list_argmax<32>(a, tab, lists[wid], nl, wv, lane, gb, xb);
+    list_argmax<32>(a, P, tab, lists[wid], nl, wv, lane, gb, xb);
     group_argmax<32>(gb, xb);
     self = warp_sum(self);
     if (lane == 0) {
       nlists[wid] = 0;
-      const long long gC = gain_self(a.m, self, wv, WC);
-      phi += gC;
-      decide(a, v, gC, xb, gb, cntL);
+      const long long gC = gain_self(P, self, wv, WC);
+      add_self(a, v, gC, phi);
+      decide(a, P, v, gC, xb, gb, cntL);
     }
     __syncwarp();
   });
   flush_block_sum(cntL, &a.sc->count_L);
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 // Bins 5-8: one block per vertex; dynamic shared memory holds the table
@@ -382,6 +412,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
     const int32_t Cv = a.C[v];
     const long long wv = a.g.vw[v];
+    const GraphParam P = a.gp[graph_of(a, v)];
     const uint32_t cap = table_cap(end - beg);
     bool ok = true;
     long long self =
@@ -392,19 +423,19 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     const int nl = nlist;
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    list_argmax<GS>(a, tab, claimed, nl, wv, threadIdx.x, gb, xb);
+    list_argmax<GS>(a, P, tab, claimed, nl, wv, threadIdx.x, gb, xb);
     Grp<GS>::argmax(gb, xb, rg, rx);
     self = Grp<GS>::sum(self, rs);
     if (threadIdx.x == 0) {
       nlist = 0;
-      const long long gC = gain_self(a.m, self, wv, WC);
-      phi += gC;
-      decide(a, v, gC, xb, gb, cntL);
+      const long long gC = gain_self(P, self, wv, WC);
+      add_self(a, v, gC, phi);
+      decide(a, P, v, gC, xb, gb, cntL);
     }
     __syncthreads();
   }
   flush_block_sum(cntL, &a.sc->count_L);
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 // --------------------------------------------------------- hubs (bin 6)
@@ -487,9 +518,10 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_scan(PassArgs a) {
   const int32_t v = a.hub.vtx[h];
   const int64_t beg = a.g.rp[v];
   const long long wv = a.g.vw[v];
+  const GraphParam P = a.gp[graph_of(a, v)];
   long long gb = LLONG_MIN;
   int32_t xb = kNone;
-  range_argmax<kHubThreads>(a, a.gtab + 2 * beg, (uint32_t)(2 * (a.hub.e0[c] - beg)),
+  range_argmax<kHubThreads>(a, P, a.gtab + 2 * beg, (uint32_t)(2 * (a.hub.e0[c] - beg)),
                             (uint32_t)(2 * (a.hub.e1[c] - beg)), wv, threadIdx.x, gb, xb);
   hub_part_store(a, c, gb, xb);
 }
@@ -499,11 +531,12 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_first(PassArgs a) {
   const int c = blockIdx.x;
   const int32_t v = a.hub.vtx[a.hub.hub_of[c]];
   const long long wv = a.g.vw[v];
+  const GraphParam P = a.gp[graph_of(a, v)];
   long long gb = LLONG_MIN;
   int32_t xb = kNone;
 #pragma unroll 4
   for (int64_t e = a.hub.e0[c] + threadIdx.x; e < a.hub.e1[c]; e += kHubThreads)
-    first_edge(a, e, wv, gb, xb);
+    first_edge(a, P, e, wv, gb, xb);
   hub_part_store(a, c, gb, xb);
 }
 
@@ -513,6 +546,7 @@ __global__ void k_hub_decide(PassArgs a, int first) {
   long long cntL = 0, phi = 0;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < a.hub.H; h += gridDim.x * blockDim.x) {
     const int32_t v = a.hub.vtx[h];
+    const GraphParam P = a.gp[graph_of(a, v)];
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
     for (int c = a.hub.c0[h]; c < a.hub.c0[h + 1]; ++c)
@@ -524,13 +558,13 @@ __global__ void k_hub_decide(PassArgs a, int first) {
     if (!first) {
       const long long self = a.hub.acc[h];
       a.hub.acc[h] = 0;
-      gC = gain_self(a.m, self, a.g.vw[v], a.W[a.C[v]]);
-      phi += gC;
+      gC = gain_self(P, self, a.g.vw[v], a.W[a.C[v]]);
+      add_self(a, v, gC, phi);
     }
-    decide(a, v, gC, xb, gb, cntL);
+    decide(a, P, v, gC, xb, gb, cntL);
   }
   flush_block_sum(cntL, &a.sc->count_L);
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 // ------------------------------------------------ afterburner (Algorithm 3)
@@ -545,14 +579,14 @@ __global__ void k_ab_prep(PassArgs a) {
     AbRec r;
     r.C = a.C[v];
     r.D = a.D[v];
-    r.q = r.D != kNone ? eps_bucket(a.m, a.delta[v]) : 0;
+    r.q = r.D != kNone ? eps_bucket(a.m, a.gp[graph_of(a, (int32_t)v)].Lam, a.delta[v]) : 0;
     a.ab[v] = r;
   }
 }
 
 struct AbCtx {
-  int32_t v, Cv, Dv;
-  long long qv, wv;
+  int32_t v, Cv, Dv, vbase;
+  long long qv, wv, mu, Lam;
   uint32_t hv;
 };
 
@@ -564,7 +598,12 @@ __device__ __forceinline__ AbCtx ab_ctx(const PassArgs &a, int32_t v) {
   c.Dv = r.D;
   c.qv = r.q;
   c.wv = a.g.vw[v];
-  c.hv = fmix32((uint32_t)v ^ a.m.seed);
+  const GraphParam P = a.gp[graph_of(a, v)];
+  c.vbase = P.vbase;
+  c.mu = P.mu;
+  c.Lam = P.Lam;
+  // the hash takes the id within the vertex's own graph
+  c.hv = fmix32((uint32_t)(v - c.vbase) ^ a.m.seed);
   return c;
 }
 
@@ -598,13 +637,15 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       need[k] = rec[k].D != kNone &&
-                earlier(rec[k].q, fmix32((uint32_t)u[k] ^ a.m.seed), u[k], c.qv, c.hv, c.v);
+                (rec[k].q != c.qv ? rec[k].q > c.qv
+                                  : earlier(rec[k].q, fmix32((uint32_t)(u[k] - c.vbase) ^ a.m.seed),
+                                            u[k], c.qv, c.hv, c.v));
       wu[k] = need[k] ? a.g.vw[u[k]] : 0;
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (!need[k]) continue;
-      const long long aw = a.m.Lam * (long long)w[k] - a.m.mu * wu[k] * c.wv;
+      const long long aw = c.Lam * (long long)w[k] - c.mu * wu[k] * c.wv;
       const int32_t Cu = rec[k].C, Du = rec[k].D;
       if (c.Cv == Cu)
         d += aw;
@@ -622,9 +663,9 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
 // For each candidate v: delta_v adjusted by every adjacent candidate u that
 // precedes v in the order; v survives iff the adjusted delta is >= 0.
 template <int GS>
-__global__ void __launch_bounds__(GS > 32 ? GS : 256)
+__global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 4)
     k_afterburner(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
-  constexpr int U = GS == 1 ? 8 : 4;
+  constexpr int U = 4;
   __shared__ long long rs[GS > 32 ? GS / 32 : 1];
   long long cntM = 0;
   const int r = Grp<GS>::rank();
@@ -691,9 +732,10 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
         if (a.C[__ldg(a.g.col + e)] == Cv) self += __ldg(a.g.ew + e);
     }
     self = Grp<GS>::sum(self, rs);
-    if (active && r == 0) phi += gain_self(a.m, self, a.g.vw[v], a.W[Cv]);
+    if (active && r == 0)
+      add_self(a, v, gain_self(a.gp[graph_of(a, v)], self, a.g.vw[v], a.W[Cv]), phi);
   });
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 __global__ void __launch_bounds__(kHubThreads) k_hub_objective(PassArgs a) {
@@ -713,9 +755,9 @@ __global__ void k_hub_obj_final(PassArgs a) {
     const int32_t v = a.hub.vtx[h];
     const long long self = a.hub.acc[h];
     a.hub.acc[h] = 0;
-    phi += gain_self(a.m, self, a.g.vw[v], a.W[a.C[v]]);
+    add_self(a, v, gain_self(a.gp[graph_of(a, v)], self, a.g.vw[v], a.W[a.C[v]]), phi);
   }
-  flush_block_sum(phi, &a.sc->phi_acc);
+  flush_block_sum(phi, &a.phi_acc[0]);
 }
 
 // ----------------------------------------------------------- update
@@ -768,15 +810,22 @@ __global__ void k_zero_if(int32_t *__restrict__ used, int64_t n, const int *k) {
        v += (int64_t)gridDim.x * blockDim.x)
     used[v] = 0;
 }
+// Per graph, the ids left unused after every other move go, ascending, to
+// that graph's empty-cluster movers in ascending vertex order.  Labels of a
+// graph stay inside its own vertex range, so the free ids of graph g and its
+// movers are both ranked from the graph's first vertex vbase:
+//   freepos[x] = free ids before x, freelist = all free ids in order,
+//   mrank[v]   = movers before v,
+//   mover v of graph g gets freelist[freepos[vbase] + mrank[v] - mrank[vbase]].
 struct FreeFlag {
   const int32_t *used;
   __device__ int32_t operator()(int64_t x) const { return used[x] == 0 ? 1 : 0; }
 };
 struct FreeEmit {
-  int32_t *freelist;
-  const int *k;
+  int32_t *freelist, *freepos;
   __device__ void operator()(int64_t x, int32_t pos, int32_t f) const {
-    if (f && pos < *k) freelist[pos] = (int32_t)x;
+    freepos[x] = pos;
+    if (f) freelist[pos] = (int32_t)x;
   }
 };
 struct MoverFlag {
@@ -784,26 +833,54 @@ struct MoverFlag {
   __device__ int32_t operator()(int64_t v) const { return E[v]; }
 };
 struct MoverEmit {
-  const int32_t *freelist;
-  int32_t *C;
-  int64_t *W;
-  const int64_t *vw;
-  int64_t n;
-  int *error;
-  __device__ void operator()(int64_t v, int32_t pos, int32_t f) const {
-    if (f) {
-      // there are always at least as many free ids as movers; a list entry
-      // outside [0, n) would be a bound violation, reported, never used
-      const int32_t x = freelist[pos];
-      if (x < 0 || x >= n) {
-        *error = 1;
-        return;
-      }
-      C[v] = x;
-      W[x] = vw[v];
-    }
-  }
+  int32_t *mrank;
+  __device__ void operator()(int64_t v, int32_t pos, int32_t) const { mrank[v] = pos; }
 };
+
+__global__ void k_assign_free(PassArgs a, const uint8_t *__restrict__ E,
+                              const int32_t *__restrict__ freelist, const int32_t *__restrict__ freepos,
+                              const int32_t *__restrict__ mrank) {
+  if (a.sc->empty_movers == 0) return;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (!E[v]) continue;
+    const int g = graph_of(a, (int32_t)v);
+    const int32_t vb = a.gp[g].vbase;
+    const int64_t idx = (int64_t)freepos[vb] + mrank[v] - mrank[vb];
+    const int32_t x = (idx >= 0 && idx < a.g.n) ? freelist[idx] : -1;
+    // there are always at least as many free ids in a graph as movers; an
+    // id outside the graph would be a bound violation, reported, not used
+    if (x < 0 || x >= a.g.n || graph_of(a, x) != g) {
+      a.sc->error = 1;
+      continue;
+    }
+    a.C[v] = x;
+    a.W[x] = a.g.vw[v];
+  }
+}
+
+// Per-graph objective of a batch: sums the recorded g(v, C[v]) by graph.
+// Lanes of a warp with the same graph are combined before the atomic.
+__global__ void k_graph_sums(PassArgs a) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.g.n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    const bool on = v < a.g.n;
+    const int g = on ? graph_of(a, (int32_t)v) : -1;
+    long long x = on ? a.gself[v] : 0;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, g);
+    const int leader = __ffs(peers) - 1;
+    // sum over peers: each lane adds its value into the leader's slot
+    __shared__ long long part[1024];
+    part[threadIdx.x] = 0;
+    __syncwarp();
+    if (on) atomicAdd((unsigned long long *)&part[(threadIdx.x & ~31) + leader], (unsigned long long)x);
+    __syncwarp();
+    if (on && (threadIdx.x & 31) == leader && part[threadIdx.x] != 0)
+      atomicAdd((unsigned long long *)&a.phi_acc[g], (unsigned long long)part[threadIdx.x]);
+    __syncwarp();
+  }
+}
 
 // ----------------------------------------------------------- best-of
 
@@ -813,24 +890,25 @@ __global__ void k_pass_begin(Scalars *sc) {
   sc->empty_movers = 0;
 }
 
-// Algorithm 2's best-of test on the objective accumulated in phi_acc.
-__global__ void k_bestof_test(Scalars *sc) {
-  const long long p = sc->phi_acc;
-  if (p > sc->phi_out) {
-    sc->phi_out = p;
-    sc->improved = 1;
-  } else {
-    sc->improved = 0;
+// Algorithm 2's best-of test, per graph, on the objective accumulated in
+// phi_acc (strict improvement keeps the earliest maximum).
+__global__ void k_bestof_test(long long *phi_acc, long long *phi_out, int *improved, int G) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const long long p = phi_acc[g];
+    if (p > phi_out[g]) {
+      phi_out[g] = p;
+      improved[g] = 1;
+    } else {
+      improved[g] = 0;
+    }
+    phi_acc[g] = 0;
   }
-  sc->phi_acc = 0;
 }
 
-__global__ void k_bestof_copy(const Scalars *sc, const int32_t *__restrict__ C,
-                              int32_t *__restrict__ C_out, int64_t n) {
-  if (!sc->improved) return;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+__global__ void k_bestof_copy(PassArgs a, int32_t *__restrict__ C_out) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
        v += (int64_t)gridDim.x * blockDim.x)
-    C_out[v] = C[v];
+    if (a.improved[graph_of(a, (int32_t)v)]) C_out[v] = a.C[v];
 }
 
 // ------------------------------------------------------------ helpers
@@ -1021,23 +1099,29 @@ int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
   return n;
 }
 
-int launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist, int32_t *scan_tmp,
-                 cudaStream_t s) {
-  k_apply<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, E);
+int launch_apply(const PassArgs &a, const ApplyScratch &w, cudaStream_t s) {
+  k_apply<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, w.E);
   const int *k = &a.sc->empty_movers;
-  k_zero_if<<<blocks_for(a.g.n, 256), 256, 0, s>>>(used, a.g.n, k);
-  k_mark_occupied<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a.C, E, used, a.g.n, k);
-  scan_apply<int32_t>(a.g.n, FreeFlag{used}, FreeEmit{freelist, k}, scan_tmp, s, k);
-  scan_apply<int32_t>(a.g.n, MoverFlag{E}, MoverEmit{freelist, a.C, a.W, a.g.vw, a.g.n, &a.sc->error},
-                      scan_tmp, s, k);
-  return 9;
+  k_zero_if<<<blocks_for(a.g.n, 256), 256, 0, s>>>(w.used, a.g.n, k);
+  k_mark_occupied<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a.C, w.E, w.used, a.g.n, k);
+  scan_apply<int32_t>(a.g.n, FreeFlag{w.used}, FreeEmit{w.freelist, w.freepos}, w.scan_tmp, s, k);
+  scan_apply<int32_t>(a.g.n, MoverFlag{w.E}, MoverEmit{w.mrank}, w.scan_tmp, s, k);
+  k_assign_free<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, w.E, w.freelist, w.freepos, w.mrank);
+  return 10;
 }
 
 void launch_pass_begin(Scalars *sc, cudaStream_t s) { k_pass_begin<<<1, 1, 0, s>>>(sc); }
 
-void launch_bestof(Scalars *sc, const int32_t *C, int32_t *C_out, int64_t n, cudaStream_t s) {
-  k_bestof_test<<<1, 1, 0, s>>>(sc);
-  k_bestof_copy<<<blocks_for(n, 256), 256, 0, s>>>(sc, C, C_out, n);
+int launch_graph_sums(const PassArgs &a, cudaStream_t s) {
+  if (!a.gself) return 0;
+  k_graph_sums<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
+  return 1;
+}
+
+int launch_bestof(const PassArgs &a, int32_t *C_out, cudaStream_t s) {
+  k_bestof_test<<<blocks_for(a.G, 256), 256, 0, s>>>(a.phi_acc, a.phi_out, a.improved, a.G);
+  k_bestof_copy<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, C_out);
+  return 2;
 }
 
 void launch_iota(int32_t *C, int64_t n, cudaStream_t s) {

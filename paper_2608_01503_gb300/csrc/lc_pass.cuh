@@ -9,6 +9,13 @@ namespace lc {
 struct PassArgs {
   LevelGraph g;
   Method m;
+  const int32_t *gid;     // graph of each vertex of a packed batch (nullptr: one graph)
+  const GraphParam *gp;   // [G] per-graph lambda, vertex base, active flag
+  int32_t G;
+  long long *gself;       // batch only: per-vertex g(v, C[v]) for the per-graph objective
+  long long *phi_acc;     // [G] objective of the clustering entering the pass
+  long long *phi_out;     // [G] objective of C_out
+  int *improved;          // [G] last best-of test
   int32_t *C;       // clustering entering the pass (updated by the apply step)
   int64_t *W;       // W(X) for X in [0, n)
   int32_t *D;       // destination of candidates; kNone for non-candidates
@@ -53,11 +60,17 @@ int launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
 int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s);
 int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
+// Scratch of the update step (all [n] of the level).
+struct ApplyScratch {
+  uint8_t *E;
+  int32_t *used, *freelist, *freepos, *mrank, *scan_tmp;
+};
 // Update step: moves, W, then ids for movers to new empty clusters.
-// E: uint8[n], used: int32[n], freelist: int32[n] scratch.
-int launch_apply(const PassArgs &a, uint8_t *E, int32_t *used, int32_t *freelist,
-                 int32_t *scan_tmp, cudaStream_t s);
-void launch_bestof(Scalars *sc, const int32_t *C, int32_t *C_out, int64_t n, cudaStream_t s);
+int launch_apply(const PassArgs &a, const ApplyScratch &w, cudaStream_t s);
+// Batch only: per-graph sums of the recorded g(v, C[v]) into phi_acc.
+int launch_graph_sums(const PassArgs &a, cudaStream_t s);
+// Per-graph best-of test and copy of improved graphs' labels into C_out.
+int launch_bestof(const PassArgs &a, int32_t *C_out, cudaStream_t s);
 void launch_iota(int32_t *C, int64_t n, cudaStream_t s);
 void launch_cluster_weights(const int32_t *C, const int64_t *vw, int64_t *W, int64_t n,
                             cudaStream_t s);

@@ -21,17 +21,44 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
+// acc[g] += x from every lane (warp-uniform call; g < 0 adds nothing).  When
+// all contributing lanes share a graph, as almost always, one atomic per warp.
+__device__ __forceinline__ void graph_add(long long *acc, int g, long long x) {
+  const bool on = g >= 0 && x != 0;
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, on);
+  if (!act) return;
+  const int leader = __ffs(act) - 1;
+  const int g0 = __shfl_sync(0xFFFFFFFFu, g, leader);
+  if (__all_sync(0xFFFFFFFFu, !on || g == g0)) {
+    const long long t = warp_sum(on ? x : 0ll);
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd((unsigned long long *)(acc + g0), (unsigned long long)t);
+  } else if (on) {
+    atomicAdd((unsigned long long *)(acc + g), (unsigned long long)x);
+  }
+}
+
 // Per-vertex part: vertex-weight sums and checks, row-pointer sanity.
-__global__ void __launch_bounds__(256) k_stats_vertices(LevelGraph g, int validate, GraphStats *st) {
+__global__ void __launch_bounds__(256) k_stats_vertices(LevelGraph g, int validate, GraphStats *st,
+                                                        const int32_t *gid, long long *Vg,
+                                                        long long *sw2g) {
   long long V = 0, sw2 = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const long long w = g.vw[v];
-    V += w;
-    sw2 += w * w;
-    if (validate && w < 0) report(st, LC_ERR_WEIGHT, v);
-    const int64_t beg = g.rp[v], end = g.rp[v + 1];
-    if (end < beg || beg < 0 || end > g.nnz) report(st, LC_ERR_ARG, v);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    long long w = 0;
+    if (v < g.n) {
+      w = g.vw[v];
+      V += w;
+      sw2 += w * w;
+      if (validate && w < 0) report(st, LC_ERR_WEIGHT, v);
+      const int64_t beg = g.rp[v], end = g.rp[v + 1];
+      if (end < beg || beg < 0 || end > g.nnz) report(st, LC_ERR_ARG, v);
+    }
+    if (gid) {
+      const int gg = v < g.n ? gid[v] : -1;
+      graph_add(Vg, gg, w);
+      graph_add(sw2g, gg, w * w);
+    }
   }
   V = warp_sum(V);
   sw2 = warp_sum(sw2);
@@ -45,13 +72,18 @@ __global__ void __launch_bounds__(256) k_stats_vertices(LevelGraph g, int valida
 // finds the row of the first by binary search on row_ptr and walks on.
 // Every index stays in range even for a malformed row_ptr (that case is
 // reported by the vertex part).
-__global__ void __launch_bounds__(256) k_stats_edges(LevelGraph g, int validate, GraphStats *st) {
+__global__ void __launch_bounds__(256) k_stats_edges(LevelGraph g, int validate, GraphStats *st,
+                                                     const int32_t *gid, long long *Tg) {
   constexpr int kChunk = 32;
   const int64_t chunks = (g.nnz + kChunk - 1) / kChunk;
   long long T = 0;
   unsigned long long f1 = 0, f2 = 0;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t cb = (int64_t)blockIdx.x * blockDim.x; cb < chunks;
+       cb += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = cb + threadIdx.x;
+    int cur_g = -1;      // graph of the edges summed into tg so far
+    long long tg = 0;
+    if (c < chunks) {
     const int64_t e0 = c * kChunk;
     const int64_t e1 = e0 + kChunk < g.nnz ? e0 + kChunk : g.nnz;
     int64_t lo = 0, hi = g.n;
@@ -72,6 +104,16 @@ __global__ void __launch_bounds__(256) k_stats_edges(LevelGraph g, int validate,
       const int32_t u = g.col[e];
       const int32_t w = g.ew[e];
       T += w;
+      if (gid) {
+        const int gv = gid[v];
+        if (gv != cur_g && cur_g >= 0) {  // chunk crosses into the next graph
+          atomicAdd((unsigned long long *)&Tg[cur_g], (unsigned long long)tg);
+          tg = 0;
+        }
+        cur_g = gv;
+        tg += w;
+        if (validate && u >= 0 && u < g.n && gid[u] != gv) report(st, LC_ERR_ARG, v);
+      }
       if (!validate) continue;
       if (u < 0 || u >= g.n) {
         report(st, LC_ERR_ARG, v);
@@ -93,6 +135,8 @@ __global__ void __launch_bounds__(256) k_stats_edges(LevelGraph g, int validate,
         f2 -= h2;
       }
     }
+    }
+    if (gid) graph_add(Tg, cur_g, tg);
   }
   T = warp_sum(T);
   f1 = warp_sum(f1);
@@ -111,15 +155,16 @@ __global__ void k_labels_in_range(const int32_t *__restrict__ C, int64_t n, int6
     if (C[v] < 0 || C[v] >= limit) report(st, LC_ERR_ARG, v);
 }
 
-void launch_stats(const LevelGraph &g, int validate, GraphStats *st, cudaStream_t s) {
+void launch_stats(const LevelGraph &g, int validate, GraphStats *st, const int32_t *gid, long long *Tg,
+                  long long *Vg, long long *sw2g, cudaStream_t s) {
   auto blocks = [](int64_t items) {
     int64_t b = (items + 255) / 256;
     if (b < 1) b = 1;
     if (b > 152 * 32) b = 152 * 32;
     return (unsigned)b;
   };
-  k_stats_vertices<<<blocks(g.n), 256, 0, s>>>(g, validate, st);
-  if (g.nnz > 0) k_stats_edges<<<blocks((g.nnz + 31) / 32), 256, 0, s>>>(g, validate, st);
+  k_stats_vertices<<<blocks(g.n), 256, 0, s>>>(g, validate, st, gid, Vg, sw2g);
+  if (g.nnz > 0) k_stats_edges<<<blocks((g.nnz + 31) / 32), 256, 0, s>>>(g, validate, st, gid, Tg);
 }
 
 void launch_labels_in_range(const int32_t *C, int64_t n, int64_t limit, GraphStats *st,

@@ -11,7 +11,7 @@ lambda = 1/sum of edge weights).  value = stored edges (nnz = 2m, the
 paper's 2m/t rate) per second of device time, summed over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload rmat22|grid256|sbm10k] [--no-cpu-baseline]
+                  [--workload rmat22|grid256|sbm10k|batched|served] [--no-cpu-baseline]
 
 Multi-GPU: one process per GPU under torchrun; a single graph does not
 shard, so each rank clusters its own replica (weak scaling, no collective on
@@ -42,6 +42,16 @@ WORKLOADS = {
                          "weights, CPM lambda=1/100"),
     "sbm10k": dict(desc="planted-partition SBM, 10,000 vertices in 100 blocks, p_in .05, p_out .0005, "
                         "unit weights, modularity, seed 0"),
+    "batched": dict(desc="4,096 independent SBMs, vertices log-uniform in [100, 100,000], blocks "
+                         "log-uniform in [2, 500], mean degree uniform in [4, 32], half of each vertex's "
+                         "degree leaving its block, unit weights, modularity; packed in one CSR and "
+                         "clustered together (lc_cluster_batch), versus one lc_cluster call per graph"),
+    "served": dict(desc="Poisson stream of clustering requests on host buffers: 70% SBM (vertices "
+                        "log-uniform in [1e3, 1e6], blocks and degree as in the batched recipe), 30% "
+                        "R-MAT (scale uniform in 10..20, edge factor 16), weights U[1,8], modularity or "
+                        "CPM lambda=1/50 with probability 1/2; served by lc_server (admission by device "
+                        "footprint, batched runs on concurrent slots) versus plain FIFO, one "
+                        "lc_cluster_host call at a time"),
 }
 
 
@@ -180,6 +190,183 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, world):
+    """Batched form: all graphs in one lc_cluster_batch call per step;
+    the plain path clusters a stratified sample one lc_cluster call at a time."""
+    import torch
+
+    import graphgen as gg
+    import paper_2608_01503_gb300 as lc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    count = args.count
+    graphs = gg.batched_sbms(count, seed=3)
+    b = gg.pack(graphs)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, col, ew, vw = t(b["row_ptr"]), t(b["col"]), t(b["ew"]), t(b["vw"])
+    labels = torch.empty(rp.numel() - 1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = lc.Options(profile=True)
+    for _ in range(args.warmup):
+        lc.lc_cluster_batch(rp, col, ew, vw, b["graph_ptr"], b["lam_num"], b["lam_den"], opts=opts,
+                            labels_out=labels)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    klaunch, kms = 0, {}
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, res = lc.lc_cluster_batch(rp, col, ew, vw, b["graph_ptr"], b["lam_num"], b["lam_den"],
+                                     opts=opts, labels_out=labels)
+        klaunch += sum(res[0]["kernel_launches"].values())
+        for k, v in res[0]["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    # plain: one lc_cluster call per graph, every 16th graph (device-resident)
+    sample = graphs[::16]
+    dg = [(t(g.row_ptr), t(g.col), t(g.ew), t(g.vw), g.lam_num, g.lam_den) for g in sample]
+    for x in dg[:4]:
+        lc.lc_cluster(*x)
+    torch.cuda.synchronize(dev)
+    p0 = time.perf_counter()
+    plain_labels = []
+    for x in dg:
+        lab, _ = lc.lc_cluster(*x)
+        plain_labels.append(lab)
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - p0
+    # identical results in both forms
+    gp = b["graph_ptr"]
+    same = all(torch.equal(labels[gp[16 * i]:gp[16 * i + 1]], plain_labels[i]) for i in range(len(sample)))
+    nnz = int(b["col"].shape[0])
+    value = count * world / (ms_step / 1000.0)
+    line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "batched", "description": WORKLOADS["batched"]["desc"], "graphs": count,
+                       "n": int(rp.numel() - 1), "nnz": nnz,
+                       "l2": "inputs larger than L2; no flush"},
+            "edges_per_s": nnz * world / (ms_step / 1000.0),
+            "plain": {"graphs_per_s": len(sample) / plain_s, "sample": f"every 16th graph ({len(sample)})",
+                      "identical_labels": bool(same)},
+            "speedup_vs_plain": value / (len(sample) / plain_s),
+            "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "clocks": clocks, "gpu_launches": int(klaunch)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
+
+
+def _served_arm(lc, reqs, arrivals, slots, max_batch):
+    """Submits reqs[i] at arrivals[i] seconds; returns (latencies, makespan, launches)."""
+    lat, done, launches = [], [], 0
+    with lc.Server(slots=slots, max_batch=max_batch) as srv:
+        ids, t_call = [], []
+        t0 = time.perf_counter()
+        for g, ta in zip(reqs, arrivals):
+            d = ta - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            t_call.append(time.perf_counter() - t0)
+            ids.append(srv.submit(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den))
+        for j, tc in zip(ids, t_call):
+            _, res, l = srv.wait(j)
+            lat.append(l)
+            done.append(tc + l)
+            launches += sum(res["kernel_launches"].values())
+    return lat, max(done) - arrivals[0], launches
+
+
+def _plain_arm(lc, reqs, arrivals):
+    """FIFO, one lc_cluster_host call at a time, starting each request when
+    it has arrived and the previous one is done."""
+    lat, launches = [], 0
+    t0 = time.perf_counter()
+    last = 0.0
+    for g, ta in zip(reqs, arrivals):
+        d = ta - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        _, res = lc.lc_cluster_host(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
+        last = time.perf_counter() - t0
+        lat.append(last - ta)
+        launches += sum(res["kernel_launches"].values())
+    return lat, last - arrivals[0], launches
+
+
+def run_served(args, rank, world):
+    """Served form: a saturated burst (all requests at once) gives graphs/s;
+    Poisson streams at rates swept around the plain path's saturated
+    throughput give p50/p99 latency for both arms."""
+    import torch
+
+    import graphgen as gg
+    import paper_2608_01503_gb300 as lc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    pool = gg.served_requests(args.pool, seed=4)
+    R = args.requests
+    reqs = [pool[i % len(pool)] for i in range(R)]
+    in_bytes = sum(16 * g.n + 8 + 8 * g.nnz for g in reqs) / R
+    out_bytes = sum(4 * g.n for g in reqs) / R
+    # warm-up: both paths, a few requests
+    for g in pool[:max(args.warmup, 3)]:
+        lc.lc_cluster_host(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
+    _served_arm(lc, pool[:max(args.warmup, 3)], [0.0] * max(args.warmup, 3), args.slots, args.max_batch)
+    torch.cuda.synchronize()
+    # plain saturated throughput (closed loop over the pool)
+    p0 = time.perf_counter()
+    for g in pool:
+        lc.lc_cluster_host(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
+    x_plain = len(pool) / (time.perf_counter() - p0)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    lat, span, launches = _served_arm(lc, reqs, [0.0] * R, args.slots, args.max_batch)
+    clocks = sampler.stop()
+    value = R * world / span
+    rates = []
+    for k, f in enumerate(float(x) for x in args.rates.split(",") if x):
+        rate = f * x_plain
+        rng = np.random.default_rng(4 + k)
+        arr = list(np.cumsum(rng.exponential(1.0 / rate, size=R)) - 0.0)
+        arr = [a - arr[0] for a in arr]
+        s_lat, s_span, _ = _served_arm(lc, reqs, arr, args.slots, args.max_batch)
+        p_lat, p_span, _ = _plain_arm(lc, reqs, arr)
+        rates.append({"rate_vs_plain": f, "offered_per_s": rate,
+                      "served": {"p50_s": _pct(s_lat, 0.5), "p99_s": _pct(s_lat, 0.99),
+                                 "graphs_per_s": R / s_span},
+                      "plain": {"p50_s": _pct(p_lat, 0.5), "p99_s": _pct(p_lat, 0.99),
+                                "graphs_per_s": R / p_span}})
+    line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": R,
+            "warmup": args.warmup, "ms_per_step": span * 1000.0 / R, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "served", "description": WORKLOADS["served"]["desc"], "requests": R,
+                       "distinct_graphs": len(pool), "slots": args.slots, "max_batch": args.max_batch,
+                       "mean_nnz": sum(g.nnz for g in reqs) / R,
+                       "l2": "each request's arrays are new to the device; no flush"},
+            "saturated": {"graphs_per_s": value, "p50_s": _pct(lat, 0.5), "p99_s": _pct(lat, 0.99),
+                          "plain_graphs_per_s": x_plain, "speedup_vs_plain": value / x_plain},
+            "rates": rates,
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": int(in_bytes),
+                    "d2h_bytes_per_step": int(out_bytes)},
+            "clocks": clocks, "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +377,13 @@ def main():
     ap.add_argument("--scale", type=int, default=None, help="override the size (R-MAT scale / grid side)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--count", type=int, default=4096, help="graphs of the batched workload")
+    ap.add_argument("--requests", type=int, default=2000, help="requests per rate (served)")
+    ap.add_argument("--pool", type=int, default=64, help="distinct request graphs (served)")
+    ap.add_argument("--rates", default="0.25,0.5,0.75,0.9,1.1",
+                    help="arrival rates as fractions of the plain path's throughput (served)")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--max-batch", type=int, default=64)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -198,6 +392,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args, rank, world)
+        return
+    if args.workload == "served":
+        run_served(args, rank, world)
         return
 
     import torch

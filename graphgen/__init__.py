@@ -228,14 +228,59 @@ def batched_sbm_params(count: int, seed: int = 3, n_lo: int = 100, n_hi: int = 1
     return out
 
 
-def batched_sbms(count: int = 4096, seed: int = 3, **kw) -> list[Graph]:
-    graphs = []
-    for (n, k, p_in, p_out, s) in batched_sbm_params(count, seed, **kw):
+def batched_sbms(count: int = 4096, seed: int = 3, threads: int | None = None, **kw) -> list[Graph]:
+    """The batched workload's graphs (generated on `threads` host threads;
+    each graph depends only on its own seed, so the result is the same)."""
+    import concurrent.futures as cf
+
+    params = batched_sbm_params(count, seed, **kw)
+
+    def one(p):
+        n, k, p_in, p_out, s = p
         rp, col, ew = sbm(n, k, p_in, p_out, s, 1, 1)
         g = modularity_inputs(rp, col, ew, name=f"sbm_n{n}_k{k}")
         g.meta.update(blocks=k, p_in=p_in, p_out=p_out, seed=s)
-        graphs.append(g)
-    return graphs
+        return g
+
+    with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
+        return list(ex.map(one, params))
+
+
+def served_request_params(count: int, seed: int = 4):
+    """Per-request recipe of the served workload: 70% SBM (n log-uniform in
+    [1e3, 1e6], blocks and degree as in the batched recipe), 30% R-MAT (scale
+    uniform in 10..20, edge factor 16); weights uniform in [1, 8]; objective
+    modularity or CPM lambda = 1/50 with probability 1/2 each."""
+    rng = np.random.default_rng(seed)
+    sbm_p = batched_sbm_params(count, seed=seed, n_lo=1_000, n_hi=1_000_000)
+    out = []
+    for r in range(count):
+        kind = "sbm" if rng.random() < 0.7 else "rmat"
+        cpm = bool(rng.random() < 0.5)
+        scale = int(rng.integers(10, 21))
+        out.append((kind, sbm_p[r] if kind == "sbm" else scale, cpm, seed * 1_000_003 + r))
+    return out
+
+
+def served_requests(count: int, seed: int = 4, threads: int | None = None) -> list[Graph]:
+    """The served workload's request graphs, in arrival order."""
+    import concurrent.futures as cf
+
+    def one(p):
+        kind, par, cpm, s = p
+        if kind == "sbm":
+            n, k, p_in, p_out, gs = par
+            rp, col, ew = sbm(n, k, p_in, p_out, gs, 1, 8)
+            name = f"sbm_n{n}_k{k}"
+        else:
+            rp, col, ew = rmat_csr(par, 16, 0.57, 0.19, 0.19, s, 1, 8)
+            name = f"rmat{par}"
+        if cpm:
+            return cpm_inputs(rp, col, ew, 1, 50, name=name + "_cpm")
+        return modularity_inputs(rp, col, ew, name=name + "_mod")
+
+    with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
+        return list(ex.map(one, served_request_params(count, seed)))
 
 
 def random_graph(n: int, p: float, seed: int, wmax: int = 1) -> tuple[np.ndarray, np.ndarray, np.ndarray]:

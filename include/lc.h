@@ -183,6 +183,42 @@ LC_API int lc_cluster_batch(const lc_csr *g, const int64_t *vertex_w, const int3
                             const int64_t *lambda_den, const lc_opts *opts, int32_t *labels_out,
                             lc_result *res);
 
+/* Clustering service (the served form).  Requests are host graphs; the
+ * server copies them on submit.  `slots` worker threads, each with its own
+ * CUDA stream on the device that was current at lc_server_create, admit
+ * queued requests in arrival order while their estimated device footprint
+ * (24 bytes per stored edge + 120 bytes per vertex + 1 MiB) fits in the
+ * unclaimed part of `hbm_budget` (0: half of the free device memory at
+ * creation; a request larger than the whole budget runs alone), up to
+ * `max_batch` per slot, and cluster each admission as one
+ * lc_cluster_batch call.  Slots run concurrently, so requests arriving while
+ * others are on the GPU start as soon as a slot and memory free up.  Every
+ * job's labels and result equal lc_cluster's for that graph alone.  opts
+ * applies to every job (its stream, trace and profile fields are ignored). */
+typedef struct lc_server lc_server;
+typedef struct {
+  int32_t slots;      /* concurrent admissions (default 4, max 64) */
+  int32_t max_batch;  /* jobs per admission (default 64) */
+  int64_t hbm_budget; /* bytes; 0 = half of the free device memory */
+  lc_opts opts;
+} lc_server_config;
+LC_API void lc_server_default_config(lc_server_config *c);
+LC_API int lc_server_create(const lc_server_config *cfg, lc_server **out);
+/* Queue one graph (HOST pointers, copied before return); *job_id names it. */
+LC_API int lc_server_submit(lc_server *s, const lc_csr *g_host, const int64_t *vertex_w,
+                            const int32_t *edge_w, int64_t lambda_num, int64_t lambda_den,
+                            int64_t *job_id);
+/* If the job is done: copy its labels (HOST int32[n], may be NULL) and result
+ * (may be NULL), report submit-to-done seconds (may be NULL), forget the job
+ * and return its status; otherwise LC_ERR_NOT_READY. */
+LC_API int lc_server_poll(lc_server *s, int64_t job_id, int32_t *labels_out, lc_result *res,
+                          double *latency_s);
+/* Like lc_server_poll but blocks until the job is done. */
+LC_API int lc_server_wait(lc_server *s, int64_t job_id, int32_t *labels_out, lc_result *res,
+                          double *latency_s);
+/* Finishes the queued and running jobs, stops the workers, frees the server. */
+LC_API int lc_server_destroy(lc_server *s);
+
 /* Same as lc_cluster with HOST buffers (pinned or pageable): copies the graph
  * to the device on opts->stream, clusters it, and copies labels_out (host
  * int32[n]) back before returning. */

@@ -13,6 +13,8 @@ Functions carry the C names:
   lc_contract       graph contraction (Algorithm 4)
   lc_objective      exact LambdaCC objective (Eq. 1)
   lc_objective_static  the same without allocating device memory
+  lc_server_*       the clustering service: submit host graphs, poll/wait
+                    for results; Server wraps it as a context manager
   lc_strerror       name of an error code
 """
 from __future__ import annotations
@@ -26,6 +28,8 @@ import numpy as np
 from . import _build
 
 _lib = None
+
+LC_ERR_NOT_READY = 11
 
 LC_K_NAMES = ["first_pass", "move", "afterburner", "apply", "objective", "contract", "other"]
 
@@ -75,9 +79,16 @@ class _Result(ctypes.Structure):
                 ("error_detail", ctypes.c_int64)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64), ("opts", _Opts)]
+
+
 EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "lc_cluster_host",
            "lc_local_move",
-           "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices"]
+           "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
+           "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
+           "lc_server_wait", "lc_server_destroy"]
 
 
 def library_path() -> str:
@@ -111,6 +122,17 @@ def load(build_if_missing: bool = True):
     lib.lc_objective_static.argtypes = [csr, P, P, i64, i64, P, opts, res]
     lib.lc_objective_static_max_vertices.argtypes = []
     lib.lc_objective_static_max_vertices.restype = ctypes.c_int64
+    srv = ctypes.c_void_p
+    lib.lc_server_default_config.argtypes = [ctypes.POINTER(_ServerConfig)]
+    lib.lc_server_default_config.restype = None
+    lib.lc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(srv)]
+    lib.lc_server_submit.argtypes = [srv, csr, P, P, i64, i64, ctypes.POINTER(i64)]
+    lib.lc_server_poll.argtypes = [srv, i64, P, res, ctypes.POINTER(ctypes.c_double)]
+    lib.lc_server_wait.argtypes = [srv, i64, P, res, ctypes.POINTER(ctypes.c_double)]
+    lib.lc_server_destroy.argtypes = [srv]
+    for f in ("lc_server_create", "lc_server_submit", "lc_server_poll", "lc_server_wait",
+              "lc_server_destroy"):
+        getattr(lib, f).restype = ctypes.c_int
     for f in ("lc_cluster", "lc_cluster_batch", "lc_cluster_host", "lc_local_move", "lc_contract",
               "lc_objective", "lc_objective_static"):
         getattr(lib, f).restype = ctypes.c_int
@@ -368,3 +390,97 @@ def lc_objective_static(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, 
                                  _dev(labels, torch.int32, "labels"), ctypes.byref(c), ctypes.byref(res))
     _check(rc, res)
     return _result(res)
+
+
+
+def lc_server_default_config() -> _ServerConfig:
+    cfg = _ServerConfig()
+    load().lc_server_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def lc_server_create(slots: int = 4, max_batch: int = 64, hbm_budget: int = 0,
+                     opts: Options | None = None) -> ctypes.c_void_p:
+    """Starts a clustering service on the current device; returns its handle."""
+    cfg = lc_server_default_config()
+    cfg.slots, cfg.max_batch, cfg.hbm_budget = slots, max_batch, hbm_budget
+    cfg.opts = _c_opts(opts, None)
+    h = ctypes.c_void_p()
+    _check(load().lc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def lc_server_submit(server, row_ptr, col, ew, vw, lambda_num: int, lambda_den: int) -> int:
+    """Queues one host graph (arrays are copied before return); returns the job id."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(ew, dtype=np.int32)
+    v = np.ascontiguousarray(vw, dtype=np.int64)
+    csr = _Csr(rp.shape[0] - 1, cl.shape[0], rp.ctypes.data, cl.ctypes.data if cl.size else None)
+    jid = ctypes.c_int64()
+    _check(load().lc_server_submit(server, ctypes.byref(csr), v.ctypes.data if v.size else None,
+                                   w.ctypes.data if w.size else None, int(lambda_num),
+                                   int(lambda_den), ctypes.byref(jid)))
+    return jid.value
+
+
+def _server_take(fn, server, jid: int, n: int):
+    lab = np.empty(max(n, 1), dtype=np.int32)
+    res = _Result()
+    lat = ctypes.c_double()
+    rc = fn(server, jid, lab.ctypes.data, ctypes.byref(res), ctypes.byref(lat))
+    if rc == LC_ERR_NOT_READY:
+        return None
+    _check(rc, res)
+    return lab[:n], _result(res), lat.value
+
+
+def lc_server_poll(server, jid: int, n: int):
+    """(labels, result, latency seconds) of a finished job, None while it runs."""
+    return _server_take(load().lc_server_poll, server, jid, n)
+
+
+def lc_server_wait(server, jid: int, n: int):
+    """Blocks until the job is done; (labels, result, latency seconds)."""
+    return _server_take(load().lc_server_wait, server, jid, n)
+
+
+def lc_server_destroy(server) -> None:
+    _check(load().lc_server_destroy(server))
+
+
+class Server:
+    """Context-manager wrapper of lc_server_*: requests are host graphs,
+    admitted by device-memory footprint into `slots` concurrent batched runs."""
+
+    def __init__(self, slots: int = 4, max_batch: int = 64, hbm_budget: int = 0,
+                 opts: Options | None = None):
+        self._h = lc_server_create(slots, max_batch, hbm_budget, opts)
+        self._n = {}
+
+    def submit(self, row_ptr, col, ew, vw, lambda_num: int, lambda_den: int) -> int:
+        jid = lc_server_submit(self._h, row_ptr, col, ew, vw, lambda_num, lambda_den)
+        self._n[jid] = len(row_ptr) - 1
+        return jid
+
+    def poll(self, jid: int):
+        got = lc_server_poll(self._h, jid, self._n[jid])
+        if got is not None:
+            del self._n[jid]
+        return got
+
+    def wait(self, jid: int):
+        got = lc_server_wait(self._h, jid, self._n[jid])
+        del self._n[jid]
+        return got
+
+    def close(self):
+        if self._h:
+            lc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

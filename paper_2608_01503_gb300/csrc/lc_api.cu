@@ -11,6 +11,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lc_contract.cuh"
@@ -82,12 +83,17 @@ struct Arena {
   }
 };
 
+// Once per device; several host threads (the server's slots) may get here
+// together, so the flag is set only after the configuration is in place.
 static void keep_pool_memory() {
-  static bool done = false;
-  if (done) return;
-  done = true;
+  static std::mutex mtx;
+  static uint64_t done_mask = 0;
   int dev = 0;
   cudaGetDevice(&dev);
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
+  std::lock_guard<std::mutex> lock(mtx);
+  if (done_mask & bit) return;
+  done_mask |= bit;
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process

@@ -57,14 +57,16 @@ def test_struct_layouts_match_c(tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "lc.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(lc_opts), sizeof(lc_result),"
-        " sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream), offsetof(lc_result, error_detail));"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(lc_opts), sizeof(lc_result),"
+        " sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream), offsetof(lc_result, error_detail),"
+        " sizeof(lc_server_config), offsetof(lc_server_config, opts));"
         "return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = list(map(int, subprocess.check_output([str(exe)]).split()))
     assert vals == [ctypes.sizeof(lc._Opts), ctypes.sizeof(lc._Result), ctypes.sizeof(lc._Event),
-                    ctypes.sizeof(lc._Csr), lc._Opts.stream.offset, lc._Result.error_detail.offset]
+                    ctypes.sizeof(lc._Csr), lc._Opts.stream.offset, lc._Result.error_detail.offset,
+                    ctypes.sizeof(lc._ServerConfig), lc._ServerConfig.opts.offset]
 
 
 def test_defaults_and_strerror(lib):
@@ -77,6 +79,9 @@ def test_defaults_and_strerror(lib):
     assert o.uncoarsen == 1 and o.validate == 1
     assert lc.lc_strerror(0) == "ok"
     assert "symmetric" in lc.lc_strerror(2)
+    cfg = lc.lc_server_default_config()
+    assert cfg.slots == 4 and cfg.max_batch == 64 and cfg.hbm_budget == 0
+    assert cfg.opts.pass_limit == 6
 
 
 def test_product_path_does_not_reference_oracle():

@@ -1,0 +1,73 @@
+"""Served form: requests submitted while others are running are admitted as
+slots and memory free up, and every job's result equals the graph clustered
+alone (and the oracle)."""
+import random
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2608_01503_gb300 as lc  # noqa: E402
+
+
+def request_graphs(seed=0, count=24):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        if k % 3 == 0:
+            out.append(gg.rmat(int(rng.integers(8, 13)), seed=k))
+        elif k % 3 == 1:
+            out.append(gg.sbm_planted(n=int(rng.integers(300, 3000)), blocks=int(rng.integers(3, 30)),
+                                      p_in=0.08, p_out=0.004, seed=k))
+        else:
+            rp, col, ew = gg.sbm(int(rng.integers(200, 2000)), 8, 0.06, 0.003, k, 1, 8)
+            out.append(gg.cpm_inputs(rp, col, ew, 1, 50))
+    return out
+
+
+@pytest.mark.parametrize("slots,budget", [(3, 0), (2, 4 << 20)])
+def test_served_results_equal_standalone(slots, budget):
+    graphs = request_graphs(seed=slots)
+    ids = [None] * len(graphs)
+    with lc.Server(slots=slots, max_batch=5, hbm_budget=budget) as srv:
+        def producer():
+            rnd = random.Random(7)
+            for k, g in enumerate(graphs):
+                ids[k] = srv.submit(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
+                time.sleep(rnd.uniform(0, 0.004))
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        results = [srv.wait(j) for j in ids]
+    for k, g in enumerate(graphs):
+        labels, res, lat = results[k]
+        ref, ores, _ = oracle.louvain_plus(g)
+        assert np.array_equal(labels, ref), k
+        assert res["phi"] == ores["phi"] and res["modularity"] == ores["modularity"], k
+        assert lat >= 0
+
+
+def test_poll_reports_not_ready_then_result():
+    g = gg.rmat(12, seed=3)
+    with lc.Server(slots=1) as srv:
+        j = srv.submit(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
+        got = None
+        for _ in range(20000):
+            got = srv.poll(j)
+            if got is not None:
+                break
+            time.sleep(0.001)
+    assert got is not None
+    ref, ores, _ = oracle.louvain_plus(g)
+    assert np.array_equal(got[0], ref) and got[1]["phi"] == ores["phi"]

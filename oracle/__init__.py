@@ -102,9 +102,14 @@ def _load():
                                      ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))]
         lib.orc_louvain_plus.argtypes = [G, P, ctypes.c_void_p, ctypes.POINTER(_Result), _CB,
                                          ctypes.c_void_p]
+        lib.orc_louvain_plus_constrained.argtypes = [G, P, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
+        lib.orc_louvain_plus_iterated.argtypes = [G, P, ctypes.c_int32, ctypes.c_void_p,
+                                                  ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
         lib.orc_free.argtypes = [ctypes.c_void_p]
         for f in (lib.orc_objective, lib.orc_gain, lib.orc_local_move, lib.orc_contract,
-                  lib.orc_louvain_plus):
+                  lib.orc_louvain_plus, lib.orc_louvain_plus_constrained,
+                  lib.orc_louvain_plus_iterated):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -258,6 +263,27 @@ def louvain_plus(g, params: Params | None = None, trace: bool = False, trace_pas
     """Algorithm 1.  Returns (labels, result dict, events).  With trace=True the
     events hold every LocalMovePasses result and coarse graph; trace_passes
     adds every pass's intermediate state."""
+    return _run(g, params, trace, trace_passes, "louvain_plus")
+
+
+def louvain_plus_constrained(g, constraint, params: Params | None = None, trace: bool = False,
+                             trace_passes: bool = False):
+    """Algorithm 1 with its coarsening constrained by the clustering
+    `constraint` (int32 >= 0 per vertex; Section V-B).  Same returns."""
+    B = np.ascontiguousarray(constraint, dtype=np.int32)
+    if B.shape[0] != g.n:
+        raise ValueError("constraint must have one entry per vertex")
+    return _run(g, params, trace, trace_passes, "louvain_plus_constrained", B)
+
+
+def louvain_plus_iterated(g, iterations: int, params: Params | None = None, trace: bool = False,
+                          trace_passes: bool = False):
+    """Iterated Louvain+ (Section V-B): `iterations` runs in total, each after
+    the first constrained by the previous output."""
+    return _run(g, params, trace, trace_passes, "louvain_plus_iterated", iterations)
+
+
+def _run(g, params, trace, trace_passes, fn, extra=None):
     p = params or Params()
     h = _graph(g)
     labels = np.zeros(max(g.n, 1), dtype=np.int32)
@@ -265,8 +291,18 @@ def louvain_plus(g, params: Params | None = None, trace: bool = False, trace_pas
     cp = _c_params(g.lam_num, g.lam_den, p)
     rec = _Recorder(passes=trace_passes)
     cb = _CB(rec) if (trace or trace_passes) else _CB(0)
-    _rc(_load().orc_louvain_plus(ctypes.byref(h.g), ctypes.byref(cp), labels.ctypes.data,
-                                 ctypes.byref(res), cb, None), "louvain_plus")
+    lib = _load()
+    if fn == "louvain_plus":
+        rc = lib.orc_louvain_plus(ctypes.byref(h.g), ctypes.byref(cp), labels.ctypes.data,
+                                  ctypes.byref(res), cb, None)
+    elif fn == "louvain_plus_constrained":
+        rc = lib.orc_louvain_plus_constrained(ctypes.byref(h.g), ctypes.byref(cp),
+                                              extra.ctypes.data if extra.size else None,
+                                              labels.ctypes.data, ctypes.byref(res), cb, None)
+    else:
+        rc = lib.orc_louvain_plus_iterated(ctypes.byref(h.g), ctypes.byref(cp), int(extra),
+                                           labels.ctypes.data, ctypes.byref(res), cb, None)
+    _rc(rc, fn)
     labels = labels[:g.n]
     out = {"n_clusters": res.n_clusters, "levels": res.levels, "passes_total": res.passes_total,
            "phi": _i128(res.phi_hi, res.phi_lo), "objective": res.objective,

@@ -198,7 +198,7 @@ static int earlier(int64_t u, int64_t v, const int64_t *q, uint32_t seed) {
 typedef struct {
   int64_t n;
   int64_t *W, *acc, *delta, *q, *adj, *gC;
-  int32_t *touched, *D, *C_before, *C_next, *mark;
+  int32_t *touched, *D, *C_before, *C_next, *mark, *Bc;
   uint8_t *in_L, *in_M;
 } work;
 
@@ -214,6 +214,7 @@ static void work_free(work *w) {
   free(w->C_before);
   free(w->C_next);
   free(w->mark);
+  free(w->Bc);
   free(w->in_L);
   free(w->in_M);
   memset(w, 0, sizeof(*w));
@@ -234,26 +235,46 @@ static int work_alloc(work *w, int64_t n) {
   w->C_before = calloc(m, 4);
   w->C_next = calloc(m, 4);
   w->mark = calloc(m, 4);
+  w->Bc = calloc(m, 4);
   w->in_L = calloc(m, 1);
   w->in_M = calloc(m, 1);
   if (!w->W || !w->acc || !w->delta || !w->q || !w->adj || !w->gC || !w->touched || !w->D ||
-      !w->C_before || !w->C_next || !w->mark || !w->in_L || !w->in_M) {
+      !w->C_before || !w->C_next || !w->mark || !w->Bc || !w->in_L || !w->in_M) {
     work_free(w);
     return ORC_ERR_OOM;
   }
   return ORC_OK;
 }
 
+#define ORC_MIXED (-1)
+
 /* One synchronous pass of Algorithm 2 (the body of its pass loop) with
  * temperature phi = phi_n / phi_d: destinations and candidate list
  * (Algorithm 2), afterburner filter (Algorithm 3), Update (apply D for M).
- * C is updated in place. */
-static void one_pass(const orc_graph *g, const orc_params *p, int32_t phi_n, int32_t phi_d,
-                     int32_t *C, work *w, int64_t *count_L, int64_t *count_M) {
+ * C is updated in place.
+ * With a constraint clustering B (Section V-B, the note on iterating
+ * Louvain+; NULL = none), v may only join a cluster X all of whose members
+ * u have B[u] = B[v]; Bc[X] holds that common value, ORC_MIXED when the
+ * members disagree (such a cluster admits nobody).  Staying and the empty
+ * cluster are always allowed. */
+static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, int32_t phi_n,
+                     int32_t phi_d, int32_t *C, work *w, int64_t *count_L, int64_t *count_M) {
   const int64_t n = g->n, mu = p->lam_num, Lam = p->lam_den;
   memcpy(w->C_before, C, (size_t)n * sizeof(int32_t));
   cluster_weights(g, C, w->W);
   int64_t nL = 0, nM = 0;
+  if (B) {
+    for (int64_t x = 0; x < n; x++) w->mark[x] = 0; /* mark: Bc[x] is set */
+    for (int64_t v = 0; v < n; v++) {
+      const int32_t X = C[v];
+      if (!w->mark[X]) {
+        w->mark[X] = 1;
+        w->Bc[X] = B[v];
+      } else if (w->Bc[X] != B[v]) {
+        w->Bc[X] = ORC_MIXED;
+      }
+    }
+  }
 
   /* Algorithm 2, parallel loop over V: D[v] = argmax over C \ C[v]. */
   for (int64_t v = 0; v < n; v++) {
@@ -271,6 +292,7 @@ static void one_pass(const orc_graph *g, const orc_params *p, int32_t phi_n, int
     for (int64_t t = 0; t < nt; t++) {
       const int32_t X = w->touched[t];
       if (X == Cv) continue;
+      if (B && (B[v] == ORC_MIXED || w->Bc[X] != B[v])) continue; /* the constraint forbids X */
       const i128 gX = (i128)Lam * w->acc[X] - (i128)mu * wv * w->W[X];
       if (best == ORC_NONE || gX > gbest || (gX == gbest && X < best)) {
         best = X;
@@ -355,8 +377,8 @@ typedef struct {
 
 /* Algorithm 2: `limit` synchronous passes from C (in/out); keeps the best
  * lambdaCC clustering seen, including the input (strict improvement). */
-static int local_move_passes(const orc_graph *g, const orc_params *p, int32_t *C, int level,
-                             int phase, tracer *tr, i128 *phi_out_ret) {
+static int local_move_passes(const orc_graph *g, const orc_params *p, const int32_t *B, int32_t *C,
+                             int level, int phase, tracer *tr, i128 *phi_out_ret) {
   const int64_t n = g->n;
   work w;
   if (work_alloc(&w, n)) return ORC_ERR_OOM;
@@ -369,7 +391,7 @@ static int local_move_passes(const orc_graph *g, const orc_params *p, int32_t *C
   i128 phi_out = objective(g, p->lam_num, p->lam_den, C, w.W);
   for (int i = 1; i <= p->pass_limit; i++) {
     int64_t nL = 0, nM = 0;
-    one_pass(g, p, p->phi_num[i - 1], p->phi_den[i - 1], C, &w, &nL, &nM);
+    one_pass(g, p, B, p->phi_num[i - 1], p->phi_den[i - 1], C, &w, &nL, &nM);
     /* one_pass leaves the afterburner arrays intact; W is reused below */
     const i128 phi = objective(g, p->lam_num, p->lam_den, C, w.W);
     if (tr) tr->passes_total++;
@@ -436,7 +458,7 @@ int orc_local_move(const orc_graph *g, const orc_params *p, int32_t *C, orc_call
     if (C[v] < 0 || C[v] >= g->n) return ORC_ERR_ARG;
   tracer tr = {cb, ctx, 0};
   i128 phi = 0;
-  rc = local_move_passes(g, p, C, 0, ORC_PHASE_COARSEN, &tr, &phi);
+  rc = local_move_passes(g, p, NULL, C, 0, ORC_PHASE_COARSEN, &tr, &phi);
   if (!rc && phi_hi && phi_lo) split128(phi, phi_hi, phi_lo);
   return rc;
 }
@@ -583,21 +605,30 @@ static int64_t compact_labels(int32_t *C, int64_t n) {
 
 /* Algorithm 1: coarsen (singleton start, LocalMovePasses, stop when every
  * cluster is a singleton, otherwise contract) then uncoarsen (project, and
- * for Louvain+ run LocalMovePasses again).  labels_out gets dense ids. */
-int orc_louvain_plus(const orc_graph *g0, const orc_params *p, int32_t *labels_out, orc_result *res,
-                     orc_callback cb, void *ctx) {
+ * for Louvain+ run LocalMovePasses again).  labels_out gets dense ids.
+ * With a constraint clustering B0 (>= 0 per vertex; NULL = none) the
+ * coarsening-phase LocalMovePasses are constrained by it (Section V-B):
+ * coarse vertex x carries the B common to its members (ORC_MIXED if they
+ * disagree), and the uncoarsening phase is unconstrained. */
+static int louvain_plus(const orc_graph *g0, const orc_params *p, const int32_t *B0,
+                        int32_t *labels_out, orc_result *res, orc_callback cb, void *ctx,
+                        int32_t passes_before) {
   int rc = check_params(g0, p);
   if (rc) return rc;
   if (!labels_out || !res) return ORC_ERR_ARG;
+  if (B0)
+    for (int64_t v = 0; v < g0->n; v++)
+      if (B0[v] < 0) return ORC_ERR_ARG;
   memset(res, 0, sizeof(*res));
-  tracer tr = {cb, ctx, 0};
+  tracer tr = {cb, ctx, passes_before};
 
   int cap = 64, L = 0;
   orc_owned_graph *coarse = calloc((size_t)cap, sizeof(orc_owned_graph)); /* G_1.. */
   int32_t **Cl = calloc((size_t)cap, sizeof(int32_t *)); /* dense C_l of each coarsened level */
+  int32_t **Bl = calloc((size_t)cap, sizeof(int32_t *)); /* constraint of each coarse level */
   orc_graph *G = calloc((size_t)cap, sizeof(orc_graph));
   int32_t *cur = NULL;
-  if (!coarse || !Cl || !G) {
+  if (!coarse || !Cl || !Bl || !G) {
     rc = ORC_ERR_OOM;
     goto out;
   }
@@ -610,7 +641,8 @@ int orc_louvain_plus(const orc_graph *g0, const orc_params *p, int32_t *labels_o
       goto out;
     }
     for (int64_t v = 0; v < n; v++) C[v] = (int32_t)v; /* SingletonClustering */
-    if ((rc = local_move_passes(&G[L], p, C, L, ORC_PHASE_COARSEN, &tr, NULL))) {
+    const int32_t *B = L == 0 ? B0 : (B0 ? Bl[L] : NULL);
+    if ((rc = local_move_passes(&G[L], p, B, C, L, ORC_PHASE_COARSEN, &tr, NULL))) {
       free(C);
       goto out;
     }
@@ -633,6 +665,27 @@ int orc_louvain_plus(const orc_graph *g0, const orc_params *p, int32_t *labels_o
     }
     Cl[L] = C;
     if ((rc = contract(&G[L], C, k, &coarse[L + 1]))) goto out;
+    if (B0) { /* B of coarse vertex x: the value its members share */
+      int32_t *Bn = malloc((size_t)k * 4);
+      uint8_t *seen = calloc((size_t)k, 1);
+      if (!Bn || !seen) {
+        free(Bn);
+        free(seen);
+        rc = ORC_ERR_OOM;
+        goto out;
+      }
+      for (int64_t v = 0; v < n; v++) {
+        const int32_t x = C[v];
+        if (!seen[x]) {
+          seen[x] = 1;
+          Bn[x] = B[v];
+        } else if (Bn[x] != B[v]) {
+          Bn[x] = ORC_MIXED;
+        }
+      }
+      free(seen);
+      Bl[L + 1] = Bn;
+    }
     G[L + 1].n = coarse[L + 1].n;
     G[L + 1].nnz = coarse[L + 1].nnz;
     G[L + 1].row_ptr = coarse[L + 1].row_ptr;
@@ -669,7 +722,7 @@ int orc_louvain_plus(const orc_graph *g0, const orc_params *p, int32_t *labels_o
     free(cur);
     cur = C;
     if (p->uncoarsen)
-      if ((rc = local_move_passes(&G[l], p, C, l, ORC_PHASE_UNCOARSEN, &tr, NULL))) goto out;
+      if ((rc = local_move_passes(&G[l], p, NULL, C, l, ORC_PHASE_UNCOARSEN, &tr, NULL))) goto out;
   }
   {
     const int64_t n = g0->n;
@@ -701,10 +754,45 @@ out:
   free(cur);
   if (Cl)
     for (int l = 0; l < cap; l++) free(Cl[l]);
+  if (Bl)
+    for (int l = 0; l < cap; l++) free(Bl[l]);
+  free(Bl);
   if (coarse)
     for (int l = 0; l < cap; l++) owned_free(&coarse[l]);
   free(Cl);
   free(coarse);
   free(G);
+  return rc;
+}
+
+int orc_louvain_plus(const orc_graph *g0, const orc_params *p, int32_t *labels_out, orc_result *res,
+                     orc_callback cb, void *ctx) {
+  return louvain_plus(g0, p, NULL, labels_out, res, cb, ctx, 0);
+}
+
+/* Louvain+ whose coarsening is constrained by the clustering B (Section
+ * V-B). */
+int orc_louvain_plus_constrained(const orc_graph *g0, const orc_params *p, const int32_t *B,
+                                 int32_t *labels_out, orc_result *res, orc_callback cb,
+                                 void *ctx) {
+  if (!B && g0 && g0->n > 0) return ORC_ERR_ARG;
+  return louvain_plus(g0, p, B, labels_out, res, cb, ctx, 0);
+}
+
+/* Iterated Louvain+ (Section V-B): the first iteration is unconstrained;
+ * every further one is constrained by the previous iteration's output.
+ * `iterations` >= 1 in total; res describes the last one, with
+ * passes_total summed over all. */
+int orc_louvain_plus_iterated(const orc_graph *g0, const orc_params *p, int32_t iterations,
+                              int32_t *labels_out, orc_result *res, orc_callback cb, void *ctx) {
+  if (!g0 || iterations < 1 || !labels_out || !res) return ORC_ERR_ARG;
+  int32_t *B = malloc((size_t)(g0->n > 0 ? g0->n : 1) * 4);
+  if (!B) return ORC_ERR_OOM;
+  int rc = louvain_plus(g0, p, NULL, labels_out, res, cb, ctx, 0);
+  for (int32_t it = 1; rc == ORC_OK && it < iterations; it++) {
+    memcpy(B, labels_out, (size_t)g0->n * 4);
+    rc = louvain_plus(g0, p, B, labels_out, res, cb, ctx, res->passes_total);
+  }
+  free(B);
   return rc;
 }

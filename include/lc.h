@@ -165,6 +165,28 @@ LC_API const char *lc_strerror(int code);
 LC_API int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
                int64_t lambda_den, const lc_opts *opts, int32_t *labels_out, lc_result *res);
 
+/* Louvain+ with a constraint clustering (Section V-B, the note on iterating
+ * Louvain+): during coarsening a vertex may only join a cluster whose
+ * members all carry its own constraint label, so every coarsening-phase
+ * cluster lies inside one class; coarse vertices carry their members'
+ * label; the uncoarsening phase is unconstrained.  constraint: device
+ * int32[n] (only equality of labels matters), read-only, caller-owned,
+ * NULL only when n = 0 (LC_ERR_ARG otherwise).  Everything else as
+ * lc_cluster. */
+LC_API int lc_cluster_constrained(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                                  int64_t lambda_num, int64_t lambda_den, const int32_t *constraint,
+                                  const lc_opts *opts, int32_t *labels_out, lc_result *res);
+
+/* Iterated Louvain+ (Section V-B): `iterations` (>= 1) runs in total; the
+ * first is lc_cluster, each further one is lc_cluster_constrained with the
+ * previous output as the constraint.  labels_out gets the last output; res
+ * describes the last run, with passes, edge counts and kernel profile
+ * summed over all runs.  Allocates one int32[n] device buffer on
+ * opts.stream for the constraint. */
+LC_API int lc_cluster_iterated(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                               int64_t lambda_num, int64_t lambda_den, int32_t iterations,
+                               const lc_opts *opts, int32_t *labels_out, lc_result *res);
+
 /* Batched Louvain+: `count` independent graphs packed into one CSR g (the
  * disjoint union, global vertex ids): graph k owns the vertex range
  * [graph_ptr[k], graph_ptr[k+1]) (graph_ptr: HOST int64[count+1], 0 first,

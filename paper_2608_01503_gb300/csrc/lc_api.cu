@@ -14,6 +14,7 @@
 #include <mutex>
 #include <vector>
 
+#include "lc_constraint.cuh"
 #include "lc_contract.cuh"
 #include "lc_internal.cuh"
 #include "lc_pass.cuh"
@@ -163,6 +164,7 @@ struct Level {
   std::vector<int64_t> vbase, nv;    // [G] host
   std::vector<uint8_t> cont;         // [G] host: graph coarsens further from this level
   int32_t *Cd = nullptr;             // [n] dense coarse id (-1: graph finished here)
+  const int32_t *B = nullptr;        // [n] constraint label (constrained coarsening), or none
 };
 
 struct Run {
@@ -456,6 +458,44 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   return LC_OK;
 }
 
+// The coarsening passes of a constrained level: the same passes run on G_l
+// without the edges between constraint classes (lc_constraint.cu states
+// why they are identical).  L keeps its full graph and bins on return.
+static int constrained_passes(Run &r, Level &L, int level, const std::vector<uint8_t> &present) {
+  const LevelGraph full = L.g;
+  const Bins full_bins = L.bins;
+  const Hubs full_hub = L.hub;
+  int64_t *rp_f = nullptr;
+  LC_TRY(r.ar.get(&rp_f, full.n + 1));
+  r.prof.begin(LC_K_OTHER);
+  launch_filter_count(full, L.B, r.cnt, r.s);
+  launch_contract_rowptr(r.cnt, full.n, rp_f, r.scan64, r.s);
+  int64_t nnz_f = 0;
+  LC_CK(cudaMemcpyAsync(&nnz_f, rp_f + full.n, sizeof(int64_t), cudaMemcpyDeviceToHost, r.s));
+  LC_CK(cudaStreamSynchronize(r.s));
+  LC_TRY(launch_check());
+  int32_t *col_f = nullptr, *ew_f = nullptr;
+  LC_TRY(r.ar.get(&col_f, nnz_f));
+  LC_TRY(r.ar.get(&ew_f, nnz_f));
+  launch_filter_copy(full, L.B, rp_f, col_f, ew_f, r.s);
+  r.prof.end(20.0 * full.nnz + 16.0 * full.n + 8.0 * nnz_f);
+  r.res->kernel_launches[LC_K_OTHER] += 5;
+  L.g = LevelGraph{full.n, nnz_f, rp_f, col_f, ew_f, full.vw};
+  int rc = bins_for(r, L);
+  int32_t *lists_f = L.bins.lists;
+  if (rc == LC_OK) rc = local_move_passes(r, L, true, level, 0, present);
+  L.g = full;
+  L.bins = full_bins;
+  L.hub = full_hub;
+  if (rc == LC_OK) {
+    r.ar.release(col_f);
+    r.ar.release(ew_f);
+    r.ar.release(rp_f);
+    if (lists_f != full_bins.lists) r.ar.release(lists_f);
+  }
+  return rc;
+}
+
 // Per-graph number of labels used by C (host nc[G]); also leaves newid
 // (global ascending numbering) and gstart on the device.
 static int count_labels(Run &r, Level &L, const int32_t *C, std::vector<int64_t> &nc, int64_t *total) {
@@ -715,11 +755,12 @@ static int level0(Run &r, Level &L, const LevelGraph &g0, const std::vector<int6
 // Algorithm 1 on every graph of the call; labels_out gets each graph's dense
 // ids 0..k-1 (numbered within the graph).
 static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t> &gptr,
-                        int32_t *labels_out) {
+                        int32_t *labels_out, const int32_t *B0 = nullptr) {
   GraphStats st{};
   LC_TRY(alloc_per_graph(r));
   std::vector<Level> lv(1);
   LC_TRY(level0(r, lv[0], g0, gptr));
+  lv[0].B = B0;
   LC_TRY(prepare(r, g0, lv[0].gid, &st));
   LC_TRY(alloc_scratch(r, g0.n, g0.nnz));
   r.top.assign(r.G, 0);
@@ -730,7 +771,10 @@ static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t>
     LC_TRY(bins_for(r, L));
     std::vector<uint8_t> present(r.G);
     for (int g = 0; g < r.G; ++g) present[g] = L.nv[g] > 0;
-    LC_TRY(local_move_passes(r, L, true, l, 0, present));
+    if (L.B)
+      LC_TRY(constrained_passes(r, L, l, present));
+    else
+      LC_TRY(local_move_passes(r, L, true, l, 0, present));
     Level N;
     bool any = false;
     LC_TRY(compact_level(r, lv[l], N, l, &any));
@@ -740,6 +784,13 @@ static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t>
     }
     lv.push_back(std::move(N));
     LC_TRY(contract_level(r, lv[l], lv[l + 1], l));
+    if (lv[l].B) {  // coarse vertices carry their members' constraint label
+      int32_t *Bc = nullptr;
+      LC_TRY(r.ar.get(&Bc, lv[l + 1].g.n));
+      launch_coarse_constraint(lv[l].Cd, lv[l].B, Bc, lv[l].g.n, r.s);
+      r.res->kernel_launches[LC_K_OTHER] += 1;
+      lv[l + 1].B = Bc;
+    }
   }
   for (int g = 0; g < r.G; ++g) {
     lc_result &res = r.res[g];
@@ -877,8 +928,13 @@ const char *lc_strerror(int code) {
   }
 }
 
-int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
-               int64_t lambda_den, const lc_opts *opts, int32_t *labels_out, lc_result *res) {
+}  // extern "C"
+
+namespace lc {
+// lc_cluster with an optional constraint clustering B (device int32[n]).
+static int cluster_single(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                          int64_t lambda_num, int64_t lambda_den, const int32_t *B,
+                          const lc_opts *opts, int32_t *labels_out, lc_result *res) {
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
   Run r((cudaStream_t)o.stream);
@@ -890,11 +946,81 @@ int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, 
     r.mu.assign(1, lambda_num);
     r.Lam.assign(1, lambda_den);
     LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
-    rc = cluster_impl(r, g0, std::vector<int64_t>{0, g->n}, labels_out);
+    rc = cluster_impl(r, g0, std::vector<int64_t>{0, g->n}, labels_out, B);
   } else if (rc == LC_OK) {
     res->lambda_den = lambda_den;
   }
   end_call(r, rc);
+  return rc;
+}
+}  // namespace lc
+
+extern "C" {
+
+int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
+               int64_t lambda_den, const lc_opts *opts, int32_t *labels_out, lc_result *res) {
+  return cluster_single(g, vertex_w, edge_w, lambda_num, lambda_den, nullptr, opts, labels_out, res);
+}
+
+int lc_cluster_constrained(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                           int64_t lambda_num, int64_t lambda_den, const int32_t *constraint,
+                           const lc_opts *opts, int32_t *labels_out, lc_result *res) {
+  if (g && g->n > 0 && !constraint) {
+    if (res) memset(res, 0, sizeof(*res));
+    return LC_ERR_ARG;
+  }
+  return cluster_single(g, vertex_w, edge_w, lambda_num, lambda_den, constraint, opts, labels_out,
+                        res);
+}
+
+int lc_cluster_iterated(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                        int64_t lambda_num, int64_t lambda_den, int32_t iterations,
+                        const lc_opts *opts, int32_t *labels_out, lc_result *res) {
+  if (!res) return LC_ERR_ARG;
+  memset(res, 0, sizeof(*res));
+  if (iterations < 1 || !g) return LC_ERR_ARG;
+  int rc = cluster_single(g, vertex_w, edge_w, lambda_num, lambda_den, nullptr, opts, labels_out, res);
+  if (rc != LC_OK || iterations == 1 || g->n == 0) return rc;
+  const lc_opts o = resolve_opts(opts);
+  const cudaStream_t s = (cudaStream_t)o.stream;
+  int32_t *B = nullptr;
+  if (cudaMallocAsync(&B, sizeof(int32_t) * (size_t)g->n, s) != cudaSuccess) {
+    cudaGetLastError();
+    memset(res, 0, sizeof(*res));
+    return LC_ERR_OOM;
+  }
+  lc_result total = *res;
+  for (int32_t it = 1; it < iterations && rc == LC_OK; ++it) {
+    if (cudaMemcpyAsync(B, labels_out, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess) {
+      rc = LC_ERR_CUDA;
+      break;
+    }
+    lc_result ri;
+    rc = cluster_single(g, vertex_w, edge_w, lambda_num, lambda_den, B, opts, labels_out, &ri);
+    if (rc != LC_OK) {
+      total = ri;
+      break;
+    }
+    const lc_result prev = total;
+    total = ri;  // clusters, levels and objective of the last iteration
+    total.passes_total += prev.passes_total;
+    total.edges_local_move += prev.edges_local_move;
+    total.edges_contract += prev.edges_contract;
+    for (int k = 0; k < LC_K_COUNT; ++k) {
+      total.kernel_ms[k] += prev.kernel_ms[k];
+      total.kernel_launches[k] += prev.kernel_launches[k];
+      total.kernel_bytes[k] += prev.kernel_bytes[k];
+    }
+  }
+  cudaFreeAsync(B, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  *res = total;
+  if (rc != LC_OK) {
+    const int64_t detail = res->error_detail;
+    memset(res, 0, sizeof(*res));
+    res->error_detail = detail;
+  }
   return rc;
 }
 

@@ -29,7 +29,7 @@ constexpr int kMaxLevels = 256;
 //   bin 5: d <= 512     64 threads, shared table of 1024 slots
 //   bin 6: d <= 1024    128 threads, shared table of 2048 slots
 //   bin 7: d <= 2048    256 threads, shared table of 4096 slots
-//   bin 8: d <= 4096    256 threads, shared table of 8192 slots
+//   bin 8: d <= 4096    256 threads, shared table of 6144 slots (load <= 2/3)
 //   bin 9: d >  4096    "hubs": the row is cut into chunks of kHubChunk edges
 //                       processed by independent blocks, aggregation in the
 //                       vertex's region of the global table (2d slots), then

@@ -225,108 +225,29 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
 
 // ------------------------------------ shared-table aggregation, bins 3-5
 
-// Shared tables stay clean between vertices: each vertex records the slots
-// it claims in a list, and its argmax walks that list (the distinct
-// neighbour clusters only) and resets those slots.  Capacity is 2 deg
-// rounded up to 32, so the load factor is at most 1/2.
+// Shared tables stay clean between vertices: a vertex's argmax scans the
+// slots [0, cap) it may have used and resets the occupied ones.  Capacity
+// is 2 deg rounded up to 32 (capped per bin), so the load factor is at most
+// 1/2 (2/3 in bin 8) and the scan touches consecutive slots.
 __device__ __forceinline__ uint32_t table_cap(int64_t deg) {
   return (uint32_t)((2 * deg + 31) & ~31ll);
 }
 
-// Inserts edges [beg, end) of v (strided by GS, loads batched U at a time)
-// into `tab`; claimed slots are appended to `list` (counter `nlist`, appends
-// warp-aggregated).  Returns this thread's part of S(v, C[v]).
-template <int GS, int U>
-__device__ __forceinline__ long long table_insert_row(const PassArgs &a, int64_t beg, int64_t end,
-                                                      int32_t Cv, unsigned long long *tab,
-                                                      uint32_t cap, uint16_t *list, int *nlist,
-                                                      int r, bool &ok) {
-  const int lane = threadIdx.x & 31;
-  long long self = 0;
-  for (int64_t base = beg; base < end; base += GS * U) {
-    int32_t u[U], w[U], X[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const int64_t e = base + k * GS + r;
-      u[k] = -1;
-      w[k] = 0;
-      if (e < end) {
-        u[k] = __ldg(a.g.col + e);
-        w[k] = __ldg(a.g.ew + e);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      bool fresh = false;
-      uint32_t slot = 0;
-      if (u[k] >= 0) {
-        if (X[k] == Cv)
-          self += w[k];
-        else
-          ok &= table_add(tab, cap, X[k], w[k], fresh, slot);
-      }
-      const unsigned fm = __ballot_sync(0xFFFFFFFFu, fresh);
-      if (fm) {
-        int basepos = 0;
-        if (lane == __ffs(fm) - 1) basepos = atomicAdd(nlist, __popc(fm));
-        basepos = __shfl_sync(0xFFFFFFFFu, basepos, __ffs(fm) - 1);
-        if (fresh) list[basepos + __popc(fm & ((1u << lane) - 1))] = (uint16_t)slot;
-      }
-    }
-  }
-  return self;
-}
-
-// Best (gain, cluster) over the claimed slots list[0 .. n) (strided by GS);
-// resets every slot it reads.
-template <int GS>
-__device__ __forceinline__ void list_argmax(const PassArgs &a, const GraphParam &P,
-                                            unsigned long long *tab, const uint16_t *list, int n,
-                                            long long wv, int r, long long &gb, int32_t &xb) {
-  constexpr int U = 4;
-  for (int base = 0; base < n; base += GS * U) {
-    unsigned long long t[U];
-    long long WX[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const int i = base + k * GS + r;
-      t[k] = kEmptySlot;
-      if (i < n) {
-        const uint32_t s = list[i];
-        t[k] = tab[s];
-        tab[s] = kEmptySlot;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < U; ++k) WX[k] = t[k] != kEmptySlot ? a.W[slot_key(t[k])] : 0;
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      if (t[k] == kEmptySlot) continue;
-      const int32_t X = slot_key(t[k]);
-      const long long g = gain_other(P, slot_val(t[k]), wv, WX[k]);
-      if (better(g, X, gb, xb)) {
-        gb = g;
-        xb = X;
-      }
-    }
-  }
-}
-
-// Best (gain, cluster) over slots [s0, s1) of a global table (strided by
-// GS), resetting the slots it reads (hub chunks).
+// Best (gain, cluster) over slots [s0, s1) of a table (strided by GS),
+// resetting the slots it reads.  g(v, X) = Lam S(v, X) - (mu w(v)) W(X),
+// with mu w(v) formed once.
 template <int GS>
 __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam &P,
                                              unsigned long long *tab, uint32_t s0, uint32_t s1,
                                              long long wv, int r, long long &gb, int32_t &xb) {
   constexpr int U = 4;
-  for (uint32_t base = s0; base < s1; base += GS * U) {
+  const long long Lam = P.Lam, muw = P.mu * wv;
+  for (uint32_t base = s0 + r; base < s1; base += GS * U) {
     unsigned long long t[U];
     long long WX[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-      const uint32_t s = base + k * GS + r;
+      const uint32_t s = base + k * GS;
       t[k] = s < s1 ? tab[s] : kEmptySlot;
       if (t[k] != kEmptySlot) tab[s] = kEmptySlot;
     }
@@ -336,7 +257,7 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam
     for (int k = 0; k < U; ++k) {
       if (t[k] == kEmptySlot) continue;
       const int32_t X = slot_key(t[k]);
-      const long long g = gain_other(P, slot_val(t[k]), wv, WX[k]);
+      const long long g = Lam * (long long)slot_val(t[k]) - muw * WX[k];
       if (better(g, X, gb, xb)) {
         gb = g;
         xb = X;
@@ -345,20 +266,149 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam
   }
 }
 
-// Bins 3-4: one warp per vertex, a per-warp shared table of SLOTS slots
-// and its claimed-slot list.
+// ------------------------------ split shared tables (warp and block bins)
+
+// A shared table kept as two 32-bit arrays: key[s] (0 = empty, else the
+// cluster id + 1) and val[s] (the weight sum S(v, X)).  Claiming a slot is
+// a 32-bit CAS on the key and every edge then adds its weight with a 32-bit
+// atomic add, which shared memory executes far faster than 64-bit CAS.
+struct SplitTab {
+  uint32_t *key;
+  int32_t *val;
+};
+
+// Sequential probing from slot s for cluster X (tag = X + 1).
+__device__ __forceinline__ bool split_probe(SplitTab t, uint32_t cap, uint32_t tag, int32_t w,
+                                            uint32_t s) {
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    uint32_t k = t.key[s];
+    if (k == 0u) k = atomicCAS(&t.key[s], 0u, tag);
+    if (k == 0u || k == tag) {
+      atomicAdd(&t.val[s], w);
+      return true;
+    }
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return false;
+}
+
+// Adds (X[k], w[k]) for every k with todo[k]: the first probe of all U
+// entries is read at once; a slot holding the key takes the weight, an
+// empty one is claimed by CAS (a CAS that finds the key takes it too), and
+// only a slot holding another key falls back to sequential probing.
+template <int U>
+__device__ __forceinline__ void split_add_batch(SplitTab t, uint32_t cap, const int32_t (&X)[U],
+                                                const int32_t (&w)[U], const bool (&todo)[U],
+                                                bool &ok) {
+  uint32_t sl[U], cur[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    sl[k] = todo[k] ? slot_of(X[k], cap) : 0;
+    cur[k] = todo[k] ? t.key[sl[k]] : 0;
+  }
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+    if (todo[k] && cur[k] == 0u) cur[k] = atomicCAS(&t.key[sl[k]], 0u, (uint32_t)X[k] + 1u);
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    if (!todo[k]) continue;
+    const uint32_t tag = (uint32_t)X[k] + 1u;
+    if (cur[k] == 0u || cur[k] == tag)
+      atomicAdd(&t.val[sl[k]], w[k]);
+    else
+      ok &= split_probe(t, cap, tag, w[k], sl[k] + 1 == cap ? 0 : sl[k] + 1);
+  }
+}
+
+// Inserts edges [beg, end) of v (strided by GS, U edges per thread at a
+// time).  Returns this thread's part of S(v, C[v]).  Indices are
+// row-relative 32-bit (a row has fewer than 2^31 entries).
+template <int GS, int U>
+__device__ __forceinline__ long long split_insert_row(const PassArgs &a, int64_t beg, int64_t end,
+                                                      int32_t Cv, SplitTab t, uint32_t cap, int r,
+                                                      bool &ok) {
+  const int32_t *__restrict__ col = a.g.col + beg;
+  const int32_t *__restrict__ ew = a.g.ew + beg;
+  const int deg = (int)(end - beg);
+  long long self = 0;
+  for (int base = r; base < deg; base += GS * U) {
+    int32_t u[U], w[U], X[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int e = base + k * GS;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < deg) {
+        u[k] = __ldg(col + e);
+        w[k] = __ldg(ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
+    bool todo[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      todo[k] = u[k] >= 0 && X[k] != Cv;
+      if (u[k] >= 0 && X[k] == Cv) self += w[k];
+    }
+    split_add_batch<U>(t, cap, X, w, todo, ok);
+  }
+  return self;
+}
+
+// Best (gain, cluster) over slots [0, cap) (strided by GS), resetting the
+// occupied ones.  g(v, X) = Lam S(v, X) - (mu w(v)) W(X).
+template <int GS>
+__device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam &P, SplitTab t,
+                                             uint32_t cap, long long wv, int r, long long &gb,
+                                             int32_t &xb) {
+  constexpr int U = 4;
+  const long long Lam = P.Lam, muw = P.mu * wv;
+  for (uint32_t base = r; base < cap; base += GS * U) {
+    uint32_t key[U];
+    int32_t S[U];
+    long long WX[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const uint32_t s = base + k * GS;
+      key[k] = s < cap ? t.key[s] : 0u;
+      S[k] = 0;
+      if (key[k] != 0u) {
+        S[k] = t.val[s];
+        t.key[s] = 0u;
+        t.val[s] = 0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) WX[k] = key[k] != 0u ? a.W[key[k] - 1u] : 0;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (key[k] == 0u) continue;
+      const int32_t X = (int32_t)(key[k] - 1u);
+      const long long g = Lam * (long long)S[k] - muw * WX[k];
+      if (better(g, X, gb, xb)) {
+        gb = g;
+        xb = X;
+      }
+    }
+  }
+}
+
+// Bins 3-4: one warp per vertex, a per-warp split shared table of SLOTS
+// slots.
 template <int SLOTS>
-__global__ void __launch_bounds__(kWarpBinWarps * 32, 5)
+__global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
     k_move_warp(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
-  constexpr int U = SLOTS / 64;  // one batch of loads covers the largest row of the bin
-  __shared__ unsigned long long tabs[kWarpBinWarps][SLOTS];
-  __shared__ uint16_t lists[kWarpBinWarps][SLOTS / 2];
-  __shared__ int nlists[kWarpBinWarps];
+  constexpr int U = SLOTS / 128;  // edges per lane per batch: 64 (bin 3) or 128 (bin 4)
+  __shared__ uint32_t keys[kWarpBinWarps][SLOTS];
+  __shared__ int32_t vals[kWarpBinWarps][SLOTS];
   long long cntL = 0, phi = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long *tab = tabs[wid];
-  for (int s = lane; s < SLOTS; s += 32) tab[s] = kEmptySlot;
-  if (lane == 0) nlists[wid] = 0;
+  const SplitTab tab{keys[wid], vals[wid]};
+  for (int s = lane; s < SLOTS; s += 32) {
+    tab.key[s] = 0u;
+    tab.val[s] = 0;
+  }
   __syncwarp();
   for_each_vertex<32>(count, [&](int64_t i, bool active) {
     if (!active) return;  // warp-uniform: the whole warp shares i
@@ -369,19 +419,16 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 5)
     const GraphParam P = a.gp[graph_of(a, v)];
     const uint32_t cap = table_cap(end - beg);
     bool ok = true;
-    long long self =
-        table_insert_row<32, U>(a, beg, end, Cv, tab, cap, lists[wid], &nlists[wid], lane, ok);
+    long long self = split_insert_row<32, U>(a, beg, end, Cv, tab, cap, lane, ok);
     if (!ok) a.sc->error = 1;
     const long long WC = lane == 0 ? a.W[Cv] : 0;
     __syncwarp();
-    const int nl = nlists[wid];
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    list_argmax<32>(a, P, tab, lists[wid], nl, wv, lane, gb, xb);
+    split_argmax<32>(a, P, tab, cap, wv, lane, gb, xb);
     group_argmax<32>(gb, xb);
     self = warp_sum(self);
     if (lane == 0) {
-      nlists[wid] = 0;
       const long long gC = gain_self(P, self, wv, WC);
       add_self(a, v, gC, phi);
       decide(a, P, v, gC, xb, gb, cntL);
@@ -392,20 +439,23 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 5)
   flush_block_sum(phi, &a.phi_acc[0]);
 }
 
-// Bins 5-8: one block per vertex; dynamic shared memory holds the table
-// (SLOTS x 8 bytes) followed by the claimed-slot list (SLOTS/2 x 2 bytes).
+// Bins 5-8: one block per vertex; dynamic shared memory holds the split
+// table (SLOTS keys, then SLOTS values).  A row uses min(2 deg rounded up
+// to 32, SLOTS) slots: bin 8 (deg <= 4096) has 6144 slots, a load factor of
+// at most 2/3, so that four blocks fit in an SM's shared memory.
 template <int GS, int SLOTS>
 __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__restrict__ list,
                                                    int64_t count) {
-  extern __shared__ unsigned long long tab[];
-  uint16_t *claimed = reinterpret_cast<uint16_t *>(tab + SLOTS);
+  extern __shared__ uint32_t smem_tab[];
+  const SplitTab tab{smem_tab, reinterpret_cast<int32_t *>(smem_tab + SLOTS)};
   __shared__ long long rs[GS / 32];
   __shared__ long long rg[GS / 32];
   __shared__ int32_t rx[GS / 32];
-  __shared__ int nlist;
   long long cntL = 0, phi = 0;
-  for (int s = threadIdx.x; s < SLOTS; s += GS) tab[s] = kEmptySlot;
-  if (threadIdx.x == 0) nlist = 0;
+  for (int s = threadIdx.x; s < SLOTS; s += GS) {
+    tab.key[s] = 0u;
+    tab.val[s] = 0;
+  }
   __syncthreads();
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int32_t v = list[i];
@@ -413,21 +463,18 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     const int32_t Cv = a.C[v];
     const long long wv = a.g.vw[v];
     const GraphParam P = a.gp[graph_of(a, v)];
-    const uint32_t cap = table_cap(end - beg);
+    const uint32_t cap = min(table_cap(end - beg), (uint32_t)SLOTS);
     bool ok = true;
-    long long self =
-        table_insert_row<GS, 8>(a, beg, end, Cv, tab, cap, claimed, &nlist, threadIdx.x, ok);
+    long long self = split_insert_row<GS, 4>(a, beg, end, Cv, tab, cap, threadIdx.x, ok);
     if (!ok) a.sc->error = 1;
     const long long WC = threadIdx.x == 0 ? a.W[Cv] : 0;
     __syncthreads();
-    const int nl = nlist;
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    list_argmax<GS>(a, P, tab, claimed, nl, wv, threadIdx.x, gb, xb);
+    split_argmax<GS>(a, P, tab, cap, wv, threadIdx.x, gb, xb);
     Grp<GS>::argmax(gb, xb, rg, rx);
     self = Grp<GS>::sum(self, rs);
     if (threadIdx.x == 0) {
-      nlist = 0;
       const long long gC = gain_self(P, self, wv, WC);
       add_self(a, v, gC, phi);
       decide(a, P, v, gC, xb, gb, cntL);
@@ -614,18 +661,22 @@ template <int GS, int U>
 __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c, int64_t e0,
                                               int64_t e1, int r) {
   long long d = 0;
-  for (int64_t base = e0; base < e1; base += (int64_t)GS * U) {
+  const int32_t *__restrict__ col = a.g.col + e0;
+  const int32_t *__restrict__ ew = a.g.ew + e0;
+  const int len = (int)(e1 - e0);
+  const long long muw = c.mu * c.wv;
+  for (int base = r; base < len; base += GS * U) {
     int32_t u[U], w[U];
     AbRec rec[U];
     long long wu[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-      const int64_t e = base + (int64_t)k * GS + r;
+      const int e = base + k * GS;
       u[k] = -1;
       w[k] = 0;
-      if (e < e1) {
-        u[k] = __ldg(a.g.col + e);
-        w[k] = __ldg(a.g.ew + e);
+      if (e < len) {
+        u[k] = __ldg(col + e);
+        w[k] = __ldg(ew + e);
       }
     }
 #pragma unroll
@@ -645,7 +696,7 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (!need[k]) continue;
-      const long long aw = c.Lam * (long long)w[k] - c.mu * wu[k] * c.wv;
+      const long long aw = c.Lam * (long long)w[k] - muw * wu[k];
       const int32_t Cu = rec[k].C, Du = rec[k].D;
       if (c.Cv == Cu)
         d += aw;
@@ -966,7 +1017,7 @@ static inline unsigned blocks_for(int64_t items, int per_block) {
 }
 
 // table (8 bytes per slot) + claimed-slot list (2 bytes per half slot)
-static constexpr int block_table_bytes(int slots) { return slots * 8 + slots; }
+static constexpr int block_table_bytes(int slots) { return slots * 8; }
 
 void configure_kernels() {
   cudaFuncSetAttribute(k_move_block<64, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -975,8 +1026,8 @@ void configure_kernels() {
                        block_table_bytes(2048));
   cudaFuncSetAttribute(k_move_block<256, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        block_table_bytes(4096));
-  cudaFuncSetAttribute(k_move_block<256, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       block_table_bytes(8192));
+  cudaFuncSetAttribute(k_move_block<256, 6144>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(6144));
 }
 
 void build_bins(const LevelGraph &g, Bins &b, int32_t *scan_tmp, cudaStream_t s) {
@@ -1058,7 +1109,7 @@ int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
   n += launch_move_block<64, 1024>(a, bin_range(b, 5, 5), s);
   n += launch_move_block<128, 2048>(a, bin_range(b, 6, 6), s);
   n += launch_move_block<256, 4096>(a, bin_range(b, 7, 7), s);
-  n += launch_move_block<256, 8192>(a, bin_range(b, 8, 8), s);
+  n += launch_move_block<256, 6144>(a, bin_range(b, 8, 8), s);
   if (a.hub.H > 0) {
     k_hub_move_insert<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     k_hub_move_scan<<<a.hub.Q, kHubThreads, 0, s>>>(a);

@@ -106,10 +106,17 @@ def _load():
                                                      ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
         lib.orc_louvain_plus_iterated.argtypes = [G, P, ctypes.c_int32, ctypes.c_void_p,
                                                   ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
+        lib.orc_pleiden.argtypes = [G, P, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Result), _CB,
+                                    ctypes.c_void_p]
+        lib.orc_local_move_alt.argtypes = [G, P, ctypes.c_void_p, i64p]
+        lib.orc_pleiden_refine.argtypes = [G, P, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+        lib.orc_rand.argtypes = [ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+        lib.orc_rand.restype = ctypes.c_uint64
         lib.orc_free.argtypes = [ctypes.c_void_p]
         for f in (lib.orc_objective, lib.orc_gain, lib.orc_local_move, lib.orc_contract,
                   lib.orc_louvain_plus, lib.orc_louvain_plus_constrained,
-                  lib.orc_louvain_plus_iterated):
+                  lib.orc_louvain_plus_iterated, lib.orc_pleiden, lib.orc_local_move_alt,
+                  lib.orc_pleiden_refine):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -283,6 +290,41 @@ def louvain_plus_iterated(g, iterations: int, params: Params | None = None, trac
     return _run(g, params, trace, trace_passes, "louvain_plus_iterated", iterations)
 
 
+def pleiden(g, params: Params | None = None, C_in=None, trace: bool = False, trace_passes: bool = False):
+    """pLeiden (Algorithm 5); with params.uncoarsen (the default) pLeiden+.
+    C_in: initial clustering (labels in [0, n)), None for singletons."""
+    C = None if C_in is None else np.ascontiguousarray(C_in, dtype=np.int32)
+    return _run(g, params, trace, trace_passes, "pleiden", C)
+
+
+def local_move_alt(g, labels, params: Params | None = None):
+    """One LocalMoveAlt call (Section V-A).  Returns (C, moves committed)."""
+    p = params or Params()
+    h = _graph(g)
+    C = np.ascontiguousarray(labels, dtype=np.int32).copy()
+    k = ctypes.c_int64()
+    _rc(_load().orc_local_move_alt(ctypes.byref(h.g), ctypes.byref(_c_params(g.lam_num, g.lam_den, p)),
+                                   C.ctypes.data, ctypes.byref(k)), "local_move_alt")
+    return C, k.value
+
+
+def pleiden_refine(g, B, level: int = 0, params: Params | None = None):
+    """One pLeidenR call (Algorithm 6) with constraint B; refined labels
+    (root ids, not compacted)."""
+    p = params or Params()
+    h = _graph(g)
+    Bc = np.ascontiguousarray(B, dtype=np.int32)
+    R = np.zeros(max(g.n, 1), dtype=np.int32)
+    _rc(_load().orc_pleiden_refine(ctypes.byref(h.g), ctypes.byref(_c_params(g.lam_num, g.lam_den, p)),
+                                   Bc.ctypes.data, int(level), R.ctypes.data), "pleiden_refine")
+    return R[:g.n]
+
+
+def rand(seed: int, level: int, stream: int, c: int) -> int:
+    """The counter-based generator of pLeidenR (SplitMix64 output function)."""
+    return int(_load().orc_rand(seed & 0xFFFFFFFF, level, stream, c))
+
+
 def _run(g, params, trace, trace_passes, fn, extra=None):
     p = params or Params()
     h = _graph(g)
@@ -299,6 +341,10 @@ def _run(g, params, trace, trace_passes, fn, extra=None):
         rc = lib.orc_louvain_plus_constrained(ctypes.byref(h.g), ctypes.byref(cp),
                                               extra.ctypes.data if extra.size else None,
                                               labels.ctypes.data, ctypes.byref(res), cb, None)
+    elif fn == "pleiden":
+        rc = lib.orc_pleiden(ctypes.byref(h.g), ctypes.byref(cp),
+                             None if extra is None or not extra.size else extra.ctypes.data,
+                             labels.ctypes.data, ctypes.byref(res), cb, None)
     else:
         rc = lib.orc_louvain_plus_iterated(ctypes.byref(h.g), ctypes.byref(cp), int(extra),
                                            labels.ctypes.data, ctypes.byref(res), cb, None)

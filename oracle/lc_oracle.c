@@ -796,3 +796,456 @@ int orc_louvain_plus_iterated(const orc_graph *g0, const orc_params *p, int32_t 
   free(B);
   return rc;
 }
+
+/* ============================================================ pLeiden ===
+ * Section V (Algorithms 5 and 6): pLeiden and pLeiden+.  The random choices
+ * of pLeidenR are drawn from a counter-based generator both sides implement
+ * from its published definition, so runs are reproducible. */
+
+/* SplitMix64's output function (Steele, Lea and Flood, 2014). */
+static uint64_t sm64_mix(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+/* Value number c of the stream (seed, level, stream): SplitMix64's output
+ * for state key + (c + 1) * golden gamma, key derived from the stream. */
+uint64_t orc_rand(uint32_t seed, int32_t level, int32_t stream, int64_t c) {
+  const uint64_t key =
+      sm64_mix(((uint64_t)seed << 32) ^ ((uint64_t)(uint32_t)level << 8) ^ (uint64_t)(uint32_t)stream);
+  return sm64_mix(key + (uint64_t)(c + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+/* LocalMoveAlt (Section V-A): every vertex that is not node-optimal (its
+ * ideal destination D[v], chosen by Algorithm 2's rules, has a strictly
+ * larger gain than staying) is listed in ascending vertex order.  The moves
+ * are applied one after another; the k-th move's exact objective change is
+ * taken after all earlier moves of the list (adjacent or not).  The prefix
+ * with the largest total change (the shortest among equals) is committed.
+ * A move to the empty cluster takes the smallest id unused at that moment;
+ * a vertex already alone keeps its id.  Returns the number committed. */
+static int64_t local_move_alt(const orc_graph *g, const orc_params *p, int32_t *C, work *w) {
+  const int64_t n = g->n, mu = p->lam_num, Lam = p->lam_den;
+  cluster_weights(g, C, w->W);
+  int64_t m = 0;
+  for (int64_t v = 0; v < n; v++) {
+    int64_t nt = 0;
+    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+      const int32_t X = C[g->col[e]];
+      if (w->acc[X] == 0) w->touched[nt++] = X;
+      w->acc[X] += g->ew[e];
+    }
+    const int32_t Cv = C[v];
+    const int64_t wv = g->vw[v];
+    const i128 gC = (i128)Lam * w->acc[Cv] - (i128)mu * wv * (w->W[Cv] - wv);
+    int32_t best = ORC_NONE;
+    i128 gbest = 0;
+    for (int64_t t = 0; t < nt; t++) {
+      const int32_t X = w->touched[t];
+      if (X == Cv) continue;
+      const i128 gX = (i128)Lam * w->acc[X] - (i128)mu * wv * w->W[X];
+      if (best == ORC_NONE || gX > gbest || (gX == gbest && X < best)) {
+        best = X;
+        gbest = gX;
+      }
+    }
+    for (int64_t t = 0; t < nt; t++) w->acc[w->touched[t]] = 0;
+    if (gC < 0 && (best == ORC_NONE || gbest < 0)) {
+      best = ORC_EMPTY;
+      gbest = 0;
+    }
+    w->D[v] = best;
+    if (best != ORC_NONE && gbest > gC) w->C_next[m++] = (int32_t)v; /* the list, ascending */
+  }
+  if (m == 0) return 0;
+  /* sequential application: W, cluster sizes and labels follow the moves */
+  int64_t *size = w->q; /* reused scratch */
+  for (int64_t x = 0; x < n; x++) size[x] = 0;
+  for (int64_t v = 0; v < n; v++) size[C[v]]++;
+  memcpy(w->C_before, C, (size_t)n * sizeof(int32_t));
+  int32_t *to = w->mark; /* label taken by the k-th move */
+  i128 cum = 0, best_cum = 0;
+  int64_t best_k = 0;
+  for (int64_t k = 0; k < m; k++) {
+    const int32_t v = w->C_next[k], Dv = w->D[v], Cv = C[v];
+    const int64_t wv = g->vw[v];
+    int64_t Sc = 0, Sd = 0;
+    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+      const int32_t X = C[g->col[e]];
+      if (X == Cv) Sc += g->ew[e];
+      if (Dv >= 0 && X == Dv) Sd += g->ew[e];
+    }
+    const i128 gC = (i128)Lam * Sc - (i128)mu * wv * (w->W[Cv] - wv);
+    const i128 gD = Dv >= 0 ? (i128)Lam * Sd - (i128)mu * wv * w->W[Dv] : 0;
+    cum += 2 * (gD - gC);
+    if (cum > best_cum) {
+      best_cum = cum;
+      best_k = k + 1;
+    }
+    int32_t t = Dv;
+    if (Dv == ORC_EMPTY) {
+      if (size[Cv] == 1) {
+        t = Cv;
+      } else {
+        int32_t x = 0;
+        while (size[x] != 0) x++; /* an unused id exists: a cluster has >= 2 members */
+        t = x;
+      }
+    }
+    to[k] = t;
+    w->W[Cv] -= wv;
+    w->W[t] += wv;
+    size[Cv]--;
+    size[t]++;
+    C[v] = t;
+  }
+  memcpy(C, w->C_before, (size_t)n * sizeof(int32_t));
+  for (int64_t k = 0; k < best_k; k++) C[w->C_next[k]] = to[k];
+  return best_k;
+}
+
+/* Effective ordering key of pLeidenR: (f, id), compared lexicographically. */
+static int key_less(uint64_t fa, int64_t a, uint64_t fb, int64_t b) {
+  return fa < fb || (fa == fb && a < b);
+}
+
+typedef struct {
+  int64_t root;
+  uint64_t f;
+  int64_t v;
+} tree_item;
+
+static int cmp_tree_item(const void *pa, const void *pb) {
+  const tree_item *a = (const tree_item *)pa, *b = (const tree_item *)pb;
+  if (a->root != b->root) return a->root < b->root ? -1 : 1;
+  if (a->f != b->f) return a->f < b->f ? -1 : 1;
+  return a->v < b->v ? -1 : (a->v > b->v);
+}
+
+/* pLeidenR (Algorithm 6) with constraint clustering B: refined labels R
+ * (each vertex gets the id of its cluster's tree root, or its own id).
+ *   U: vertices with w'(u, B[u] minus u) >= 0 (Lambda-scaled g(u, B[u]) >= 0).
+ *   H[v]: for v in U, a uniformly chosen member of the candidate list
+ *     [v] followed by the neighbours u in row order with u in U,
+ *     B[u] = B[v] and w'(u,v) = w(u,v) - lambda w(u) w(v) >= 0
+ *     (value 0 of stream 0, modulo the list length); v itself = no edge.
+ *   f(v) in [0, K), K = 2^62: value of stream 1, shifted right by 2.
+ *   The edge v -> H[v] is kept iff (f(H[v]), H[v]) < (f(v), v).  A vertex
+ *   with an edge that is neither kept nor any kept edge's target (a
+ *   singleton tree that did not choose itself) takes f = 2K - f and its
+ *   edge is tested again against its target's (possibly changed) key.
+ *   Trees are followed to their roots; each tree is visited in increasing
+ *   (f, id) (parents come first), and vertex t_k joins the cluster of
+ *   t_1..t_(k-1) while w'(t_k, cluster) >= 0 and w'(cluster, B minus
+ *   cluster) >= 0 (Leiden's well-connectedness); from the first failure on
+ *   the tree's vertices stay singletons. */
+static int pleiden_refine(const orc_graph *g, const orc_params *p, const int32_t *B, int32_t level,
+                          int32_t *R) {
+  const int64_t n = g->n, mu = p->lam_num, Lam = p->lam_den;
+  const size_t m = (size_t)(n > 0 ? n : 1);
+  int64_t *WB = calloc(m, 8), *SB = calloc(m, 8), *H = malloc(m * 8), *root = malloc(m * 8);
+  int64_t *pos = malloc(m * 8);
+  uint64_t *f = malloc(m * 8);
+  uint8_t *inU = calloc(m, 1), *kept = calloc(m, 1), *child = calloc(m, 1);
+  tree_item *items = malloc(m * sizeof(tree_item));
+  int rc = ORC_OK;
+  if (!WB || !SB || !H || !root || !pos || !f || !inU || !kept || !child || !items) {
+    rc = ORC_ERR_OOM;
+    goto out;
+  }
+  const uint64_t K = (uint64_t)1 << 62;
+  for (int64_t v = 0; v < n; v++) WB[B[v]] += g->vw[v];
+  for (int64_t v = 0; v < n; v++) {
+    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++)
+      if (B[g->col[e]] == B[v]) SB[v] += g->ew[e];
+    inU[v] = (i128)Lam * SB[v] - (i128)mu * g->vw[v] * (WB[B[v]] - g->vw[v]) >= 0;
+    f[v] = orc_rand(p->seed, level, 1, v) >> 2;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    H[v] = v;
+    if (!inU[v]) continue;
+    int64_t cnt = 1;
+    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+      const int64_t u = g->col[e];
+      if (inU[u] && B[u] == B[v] &&
+          (i128)Lam * g->ew[e] - (i128)mu * g->vw[u] * g->vw[v] >= 0)
+        cnt++;
+    }
+    int64_t pick = (int64_t)(orc_rand(p->seed, level, 0, v) % (uint64_t)cnt);
+    if (pick == 0) continue; /* v itself */
+    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+      const int64_t u = g->col[e];
+      if (inU[u] && B[u] == B[v] &&
+          (i128)Lam * g->ew[e] - (i128)mu * g->vw[u] * g->vw[v] >= 0) {
+        if (--pick == 0) {
+          H[v] = u;
+          break;
+        }
+      }
+    }
+  }
+  for (int64_t v = 0; v < n; v++) {
+    kept[v] = H[v] != v && key_less(f[H[v]], H[v], f[v], v);
+    if (kept[v]) child[H[v]] = 1;
+  }
+  for (int64_t v = 0; v < n; v++) /* singleton trees that chose an edge */
+    if (H[v] != v && !kept[v] && !child[v]) f[v] = 2 * K - f[v];
+  for (int64_t v = 0; v < n; v++)
+    if (H[v] != v && !kept[v] && !child[v]) kept[v] = key_less(f[H[v]], H[v], f[v], v);
+  for (int64_t v = 0; v < n; v++) {
+    int64_t r = v, steps = 0;
+    while (kept[r]) {
+      r = H[r];
+      if (++steps > n) { /* impossible: keys strictly decrease along kept edges */
+        rc = ORC_ERR_ARG;
+        goto out;
+      }
+    }
+    root[v] = r;
+  }
+  for (int64_t v = 0; v < n; v++) items[v] = (tree_item){root[v], f[v], v};
+  qsort(items, (size_t)n, sizeof(tree_item), cmp_tree_item);
+  for (int64_t i = 0; i < n; i++) pos[items[i].v] = i;
+  for (int64_t i = 0; i < n;) {
+    int64_t j = i;
+    while (j < n && items[j].root == items[i].root) j++;
+    const int64_t r = items[i].root;
+    const int64_t t1 = items[i].v;
+    R[t1] = (int32_t)t1;
+    int64_t Wc = g->vw[t1], Ec = SB[t1];
+    int ok = 1;
+    for (int64_t k = i + 1; k < j; k++) {
+      const int64_t v = items[k].v;
+      if (ok) {
+        int64_t Sv = 0; /* edges to the earlier vertices of the tree */
+        for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+          const int64_t u = g->col[e];
+          if (root[u] == r && pos[u] < k) Sv += g->ew[e];
+        }
+        const int c1 = (i128)Lam * Sv - (i128)mu * g->vw[v] * Wc >= 0;
+        const int c2 = (i128)Lam * Ec - (i128)mu * Wc * (WB[B[v]] - Wc) >= 0;
+        if (c1 && c2) {
+          R[v] = (int32_t)t1;
+          Ec += SB[v] - 2 * Sv;
+          Wc += g->vw[v];
+          continue;
+        }
+        ok = 0;
+      }
+      R[v] = (int32_t)v;
+    }
+    i = j;
+  }
+out:
+  free(WB);
+  free(SB);
+  free(H);
+  free(root);
+  free(pos);
+  free(f);
+  free(inU);
+  free(kept);
+  free(child);
+  free(items);
+  return rc;
+}
+
+/* pLeiden (Algorithm 5); with p->uncoarsen, pLeiden+ (LocalMovePasses
+ * after each projection).  C_in: initial clustering (labels in [0, n)),
+ * NULL for singletons.  Per level: LocalMovePasses from C_l; LocalMoveAlt
+ * when they left Phi unchanged; stop when every cluster is a singleton;
+ * otherwise refine (pLeidenR with B = C_l, the level as stream), contract
+ * on the refinement, and Downsample: coarse vertex x starts in the cluster
+ * of C_l its members share.  A refinement that merges nothing also ends
+ * the coarsening (contracting it would reproduce G_l).  labels_out gets
+ * dense ids; res as for orc_louvain_plus. */
+int orc_pleiden(const orc_graph *g0, const orc_params *p, const int32_t *C_in, int32_t *labels_out,
+                orc_result *res, orc_callback cb, void *ctx) {
+  int rc = check_params(g0, p);
+  if (rc) return rc;
+  if (!labels_out || !res) return ORC_ERR_ARG;
+  if (C_in)
+    for (int64_t v = 0; v < g0->n; v++)
+      if (C_in[v] < 0 || C_in[v] >= g0->n) return ORC_ERR_ARG;
+  memset(res, 0, sizeof(*res));
+  tracer tr = {cb, ctx, 0};
+  int cap = 64, L = 0;
+  orc_owned_graph *coarse = calloc((size_t)cap, sizeof(orc_owned_graph));
+  int32_t **Rl = calloc((size_t)cap, sizeof(int32_t *)); /* dense refinement of each level */
+  orc_graph *G = calloc((size_t)cap, sizeof(orc_graph));
+  int32_t *C = NULL;
+  work w;
+  memset(&w, 0, sizeof(w));
+  if (!coarse || !Rl || !G) {
+    rc = ORC_ERR_OOM;
+    goto out;
+  }
+  G[0] = *g0;
+  C = malloc((size_t)(g0->n > 0 ? g0->n : 1) * 4);
+  if (!C) {
+    rc = ORC_ERR_OOM;
+    goto out;
+  }
+  for (int64_t v = 0; v < g0->n; v++) C[v] = C_in ? C_in[v] : (int32_t)v;
+  for (;;) {
+    const int64_t n = G[L].n;
+    i128 phi_in = 0, phi_out = 0;
+    {
+      int64_t *Ws = malloc((size_t)(n > 0 ? n : 1) * 8);
+      if (!Ws) {
+        rc = ORC_ERR_OOM;
+        goto out;
+      }
+      phi_in = objective(&G[L], p->lam_num, p->lam_den, C, Ws);
+      free(Ws);
+    }
+    if ((rc = local_move_passes(&G[L], p, NULL, C, L, ORC_PHASE_COARSEN, &tr, &phi_out))) goto out;
+    if (phi_out == phi_in) {
+      if (work_alloc(&w, n)) {
+        rc = ORC_ERR_OOM;
+        goto out;
+      }
+      local_move_alt(&G[L], p, C, &w);
+      work_free(&w);
+    }
+    const int64_t k = compact_labels(C, n);
+    if (k < 0) {
+      rc = ORC_ERR_OOM;
+      goto out;
+    }
+    if (k == n) break;
+    if (L + 1 >= cap) {
+      rc = ORC_ERR_ARG;
+      goto out;
+    }
+    int32_t *R = malloc((size_t)n * 4);
+    if (!R) {
+      rc = ORC_ERR_OOM;
+      goto out;
+    }
+    if ((rc = pleiden_refine(&G[L], p, C, L, R))) {
+      free(R);
+      goto out;
+    }
+    const int64_t kr = compact_labels(R, n);
+    if (kr < 0 || kr == n) {
+      free(R);
+      if (kr < 0) rc = ORC_ERR_OOM;
+      if (rc) goto out;
+      break;
+    }
+    Rl[L] = R;
+    if ((rc = contract(&G[L], R, kr, &coarse[L + 1]))) goto out;
+    G[L + 1].n = coarse[L + 1].n;
+    G[L + 1].nnz = coarse[L + 1].nnz;
+    G[L + 1].row_ptr = coarse[L + 1].row_ptr;
+    G[L + 1].col = coarse[L + 1].col;
+    G[L + 1].ew = coarse[L + 1].ew;
+    G[L + 1].vw = coarse[L + 1].vw;
+    if (cb) {
+      orc_event ev;
+      memset(&ev, 0, sizeof(ev));
+      ev.kind = ORC_EV_CONTRACT;
+      ev.level = L;
+      ev.n = n;
+      ev.C = R;
+      ev.cn = G[L + 1].n;
+      ev.cnnz = G[L + 1].nnz;
+      ev.c_row_ptr = G[L + 1].row_ptr;
+      ev.c_col = G[L + 1].col;
+      ev.c_ew = G[L + 1].ew;
+      ev.c_vw = G[L + 1].vw;
+      cb(ctx, &ev);
+    }
+    /* Downsample: coarse vertex x starts in the C_l cluster of its members */
+    int32_t *Cn = malloc((size_t)kr * 4);
+    if (!Cn) {
+      rc = ORC_ERR_OOM;
+      goto out;
+    }
+    for (int64_t v = 0; v < n; v++) Cn[R[v]] = C[v];
+    if (compact_labels(Cn, kr) < 0) {
+      free(Cn);
+      rc = ORC_ERR_OOM;
+      goto out;
+    }
+    free(C);
+    C = Cn;
+    L++;
+  }
+  res->levels = L + 1;
+  for (int l = L - 1; l >= 0; l--) { /* ProjectCluster, and for pLeiden+ LocalMovePasses */
+    const int64_t n = G[l].n;
+    int32_t *Cp = malloc((size_t)(n > 0 ? n : 1) * 4);
+    if (!Cp) {
+      rc = ORC_ERR_OOM;
+      goto out;
+    }
+    for (int64_t v = 0; v < n; v++) Cp[v] = C[Rl[l][v]];
+    free(C);
+    C = Cp;
+    if (p->uncoarsen)
+      if ((rc = local_move_passes(&G[l], p, NULL, C, l, ORC_PHASE_UNCOARSEN, &tr, NULL))) goto out;
+  }
+  {
+    const int64_t n = g0->n;
+    const int64_t k = compact_labels(C, n);
+    int64_t *W = malloc((size_t)(n > 0 ? n : 1) * 8);
+    if (k < 0 || !W) {
+      free(W);
+      rc = ORC_ERR_OOM;
+      goto out;
+    }
+    memcpy(labels_out, C, (size_t)n * 4);
+    res->n_clusters = k;
+    const i128 phi = objective(g0, p->lam_num, p->lam_den, C, W);
+    free(W);
+    split128(phi, &res->phi_hi, &res->phi_lo);
+    i128 sw2 = 0, T = 0;
+    for (int64_t v = 0; v < n; v++) sw2 += (i128)g0->vw[v] * g0->vw[v];
+    for (int64_t e = 0; e < g0->nnz; e++) T += g0->ew[e];
+    res->objective = (double)(int64_t)phi / (double)p->lam_den;
+    res->modularity = T > 0 ? (double)(int64_t)(phi - (i128)p->lam_num * sw2) /
+                                  ((double)p->lam_den * (double)(int64_t)T)
+                            : 0.0;
+    res->passes_total = tr.passes_total;
+  }
+out:
+  work_free(&w);
+  free(C);
+  if (Rl)
+    for (int l = 0; l < cap; l++) free(Rl[l]);
+  if (coarse)
+    for (int l = 0; l < cap; l++) owned_free(&coarse[l]);
+  free(Rl);
+  free(coarse);
+  free(G);
+  return rc;
+}
+
+/* Test hooks: one LocalMoveAlt call and one pLeidenR call on level `level`. */
+int orc_local_move_alt(const orc_graph *g, const orc_params *p, int32_t *C, int64_t *committed) {
+  int rc = check_params(g, p);
+  if (rc) return rc;
+  for (int64_t v = 0; v < g->n; v++)
+    if (C[v] < 0 || C[v] >= g->n) return ORC_ERR_ARG;
+  work w;
+  if (work_alloc(&w, g->n)) return ORC_ERR_OOM;
+  const int64_t k = local_move_alt(g, p, C, &w);
+  work_free(&w);
+  if (committed) *committed = k;
+  return ORC_OK;
+}
+
+int orc_pleiden_refine(const orc_graph *g, const orc_params *p, const int32_t *B, int32_t level,
+                       int32_t *R) {
+  int rc = check_params(g, p);
+  if (rc) return rc;
+  for (int64_t v = 0; v < g->n; v++)
+    if (B[v] < 0 || B[v] >= g->n) return ORC_ERR_ARG;
+  return pleiden_refine(g, p, B, level, R);
+}

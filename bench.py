@@ -55,6 +55,11 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes per step of a kernel class, from one ncu capture of the same
+# kernels on the same workload (profiles/dram_rmat22.md); null elsewhere.
+TRAFFIC_PER_STEP = {("rmat22", "move"): 46.153e9}
+
+
 def make_graph(name: str, scale_override: int | None = None):
     import graphgen as gg
 
@@ -190,19 +195,46 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _dist_init(world, local):
+    """NCCL process group for N > 1 (barriers and the max over ranks only)."""
+    if world == 1:
+        return None
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist
+
+
+def _max_over_ranks(dist, x, dev):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_batched(args, rank, world):
     """Batched form: all graphs in one lc_cluster_batch call per step;
-    the plain path clusters a stratified sample one lc_cluster call at a time."""
+    the plain path clusters a stratified sample one lc_cluster call at a time.
+    With N ranks each clusters its share of the graphs (longest-processing-
+    time by expected stored edges); no collective touches the data."""
     import torch
 
     import graphgen as gg
     import paper_2608_01503_gb300 as lc
+    from paper_2608_01503_gb300 import shard
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = _dist_init(world, local)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     count = args.count
-    graphs = gg.batched_sbms(count, seed=3)
+    mine = shard.local([gg.expected_nnz(p) for p in gg.batched_sbm_params(count, seed=3)], rank, world)
+    graphs = gg.batched_sbms(count, seed=3, indices=mine)
     b = gg.pack(graphs)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     rp, col, ew, vw = t(b["row_ptr"]), t(b["col"]), t(b["ew"]), t(b["vw"])
@@ -216,6 +248,9 @@ def run_batched(args, rank, world):
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     klaunch, kms = 0, {}
     ev0.record(stream)
@@ -227,8 +262,10 @@ def run_batched(args, rank, world):
             kms[k] = kms.get(k, 0.0) + v
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
     clocks = sampler.stop()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
+    ms_step = _max_over_ranks(dist, ev0.elapsed_time(ev1) / args.steps, dev)
     # plain: one lc_cluster call per graph, every 16th graph (device-resident)
     sample = graphs[::16]
     dg = [(t(g.row_ptr), t(g.col), t(g.ew), t(g.vw), g.lam_num, g.lam_den) for g in sample]
@@ -246,14 +283,19 @@ def run_batched(args, rank, world):
     gp = b["graph_ptr"]
     same = all(torch.equal(labels[gp[16 * i]:gp[16 * i + 1]], plain_labels[i]) for i in range(len(sample)))
     nnz = int(b["col"].shape[0])
-    value = count * world / (ms_step / 1000.0)
+    if dist:  # stored edges of all ranks' graphs
+        t_nnz = torch.tensor([nnz], dtype=torch.int64, device=dev)
+        dist.all_reduce(t_nnz)
+        nnz = int(t_nnz.item())
+    value = count / (ms_step / 1000.0)
     line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "batched", "description": WORKLOADS["batched"]["desc"], "graphs": count,
-                       "n": int(rp.numel() - 1), "nnz": nnz,
+                       "n_rank0": int(rp.numel() - 1), "nnz": nnz,
+                       "sharding": "graphs split over ranks by expected edges (LPT); no data collective",
                        "l2": "inputs larger than L2; no flush"},
-            "edges_per_s": nnz * world / (ms_step / 1000.0),
+            "edges_per_s": nnz / (ms_step / 1000.0),
             "plain": {"graphs_per_s": len(sample) / plain_s, "sample": f"every 16th graph ({len(sample)})",
                       "identical_labels": bool(same)},
             "speedup_vs_plain": value / (len(sample) / plain_s),
@@ -261,6 +303,8 @@ def run_batched(args, rank, world):
             "clocks": clocks, "gpu_launches": int(klaunch)}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def _pct(xs, q):
@@ -308,43 +352,72 @@ def _plain_arm(lc, reqs, arrivals):
 def run_served(args, rank, world):
     """Served form: a saturated burst (all requests at once) gives graphs/s;
     Poisson streams at rates swept around the plain path's saturated
-    throughput give p50/p99 latency for both arms."""
+    throughput give p50/p99 latency for both arms.  With N ranks, request i
+    goes to rank i mod N (each rank runs its own server on its GPU); the
+    latencies are gathered on the host after each arm."""
     import torch
 
     import graphgen as gg
     import paper_2608_01503_gb300 as lc
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    dist = _dist_init(world, local)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
     pool = gg.served_requests(args.pool, seed=4)
     R = args.requests
-    reqs = [pool[i % len(pool)] for i in range(R)]
-    in_bytes = sum(16 * g.n + 8 + 8 * g.nnz for g in reqs) / R
-    out_bytes = sum(4 * g.n for g in reqs) / R
+    reqs_all = [pool[i % len(pool)] for i in range(R)]
+    reqs = reqs_all[rank::world]
+    in_bytes = sum(16 * g.n + 8 + 8 * g.nnz for g in reqs_all) / R
+    out_bytes = sum(4 * g.n for g in reqs_all) / R
+
+    def all_lat(x):
+        if dist is None:
+            return x
+        parts = [None] * world
+        dist.all_gather_object(parts, x)
+        return [v for p in parts for v in p]
+
     # warm-up: both paths, a few requests
     for g in pool[:max(args.warmup, 3)]:
         lc.lc_cluster_host(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
     _served_arm(lc, pool[:max(args.warmup, 3)], [0.0] * max(args.warmup, 3), args.slots, args.max_batch)
     torch.cuda.synchronize()
-    # plain saturated throughput (closed loop over the pool)
+    # plain saturated throughput (closed loop over the pool), all ranks together
+    if dist:
+        dist.barrier()
     p0 = time.perf_counter()
-    for g in pool:
+    for g in pool[rank::world]:
         lc.lc_cluster_host(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den)
-    x_plain = len(pool) / (time.perf_counter() - p0)
+    x_plain = len(pool) / _max_over_ranks(dist, time.perf_counter() - p0, dev)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    lat, span, launches = _served_arm(lc, reqs, [0.0] * R, args.slots, args.max_batch)
+    if dist:
+        dist.barrier()
+    lat, span, launches = _served_arm(lc, reqs, [0.0] * len(reqs), args.slots, args.max_batch)
+    span = _max_over_ranks(dist, span, dev)
+    lat = all_lat(lat)
     clocks = sampler.stop()
-    value = R * world / span
+    value = R / span
     rates = []
     for k, f in enumerate(float(x) for x in args.rates.split(",") if x):
         rate = f * x_plain
         rng = np.random.default_rng(4 + k)
-        arr = list(np.cumsum(rng.exponential(1.0 / rate, size=R)) - 0.0)
-        arr = [a - arr[0] for a in arr]
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=R))
+        arr = [float(a - arr[0]) for a in arr][rank::world]
+        t0 = arr[0] if arr else 0.0
+        arr = [a - t0 for a in arr]
+        if dist:
+            dist.barrier()
         s_lat, s_span, _ = _served_arm(lc, reqs, arr, args.slots, args.max_batch)
+        s_span = _max_over_ranks(dist, s_span, dev)
+        s_lat = all_lat(s_lat)
+        if dist:
+            dist.barrier()
         p_lat, p_span, _ = _plain_arm(lc, reqs, arr)
+        p_span = _max_over_ranks(dist, p_span, dev)
+        p_lat = all_lat(p_lat)
         rates.append({"rate_vs_plain": f, "offered_per_s": rate,
                       "served": {"p50_s": _pct(s_lat, 0.5), "p99_s": _pct(s_lat, 0.99),
                                  "graphs_per_s": R / s_span},
@@ -352,10 +425,11 @@ def run_served(args, rank, world):
                                 "graphs_per_s": R / p_span}})
     line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": R,
             "warmup": args.warmup, "ms_per_step": span * 1000.0 / R, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "served", "description": WORKLOADS["served"]["desc"], "requests": R,
                        "distinct_graphs": len(pool), "slots": args.slots, "max_batch": args.max_batch,
-                       "mean_nnz": sum(g.nnz for g in reqs) / R,
+                       "mean_nnz": sum(g.nnz for g in reqs_all) / R,
+                       "sharding": "request i served by rank i mod N; no data collective",
                        "l2": "each request's arrays are new to the device; no flush"},
             "saturated": {"graphs_per_s": value, "p50_s": _pct(lat, 0.5), "p99_s": _pct(lat, 0.99),
                           "plain_graphs_per_s": x_plain, "speedup_vs_plain": value / x_plain},
@@ -365,6 +439,8 @@ def run_served(args, rank, world):
             "clocks": clocks, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def main():
@@ -500,7 +576,10 @@ def main():
     achieved = kbytes[dom] / (kms[dom] / 1000.0) / 1e9 if kms[dom] > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (hbm_gbs)",
-                "traffic": None, "launches": klaunch[dom],
+                "traffic": (TRAFFIC_PER_STEP.get((args.workload, dom))
+                            if args.scale is None and K == 1 else None),
+                "traffic_unit": "DRAM bytes per step, all launches of the class (ncu)",
+                "launches": klaunch[dom],
                 "algorithmic_bytes_per_step": kbytes[dom] / args.steps}
     breakdown = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
                      "algorithmic_GBps": (kbytes[k] / (kms[k] / 1000.0) / 1e9) if kms[k] > 0 else None}

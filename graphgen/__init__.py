@@ -228,12 +228,23 @@ def batched_sbm_params(count: int, seed: int = 3, n_lo: int = 100, n_hi: int = 1
     return out
 
 
-def batched_sbms(count: int = 4096, seed: int = 3, threads: int | None = None, **kw) -> list[Graph]:
+def expected_nnz(p) -> float:
+    """Expected stored edges of one batched-recipe SBM (n, blocks, p_in, p_out, seed)."""
+    n, k, p_in, p_out, _ = p
+    s = n / k
+    return n * (p_in * max(s - 1.0, 0.0) + p_out * (n - s))
+
+
+def batched_sbms(count: int = 4096, seed: int = 3, threads: int | None = None,
+                 indices=None, **kw) -> list[Graph]:
     """The batched workload's graphs (generated on `threads` host threads;
-    each graph depends only on its own seed, so the result is the same)."""
+    each graph depends only on its own seed, so the result is the same).
+    With `indices`, only those graphs of the workload, in that order."""
     import concurrent.futures as cf
 
     params = batched_sbm_params(count, seed, **kw)
+    if indices is not None:
+        params = [params[i] for i in indices]
 
     def one(p):
         n, k, p_in, p_out, s = p

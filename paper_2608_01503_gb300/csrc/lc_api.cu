@@ -425,7 +425,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     }
     r.prof.begin(LC_K_AFTERBURNER);
     r.res->kernel_launches[LC_K_AFTERBURNER] += launch_afterburner(a, L.bins, r.s);
-    r.prof.end(5.0 * n);
+    r.prof.end(32.0 * n);  // + 24 B per candidate edge, added from sc->cand_edges at the end
     r.prof.begin(LC_K_APPLY);
     r.res->kernel_launches[LC_K_APPLY] += launch_apply(a, w, r.s);
     r.prof.end(14.0 * n);
@@ -855,6 +855,12 @@ static void end_call(Run &r, int rc) {
   if (r.prof.on) {
     cudaStreamSynchronize(r.s);
     r.prof.finish(r.res);
+    long long cand = 0;  // afterburner: col, ew and the 16-byte record of each candidate edge
+    if (r.sc &&
+        cudaMemcpyAsync(&cand, &r.sc->cand_edges, sizeof(cand), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
+        cudaStreamSynchronize(r.s) == cudaSuccess)
+      r.res->kernel_bytes[LC_K_AFTERBURNER] += 24.0 * (double)cand;
+    cudaGetLastError();
   }
   if (rc != LC_OK) {
     int64_t detail = r.res->error_detail;

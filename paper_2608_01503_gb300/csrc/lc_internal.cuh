@@ -94,6 +94,7 @@ struct Scalars {
   long long count_L, count_M;
   int error;             // internal bound violation (hash probe overrun)
   int pad;
+  long long cand_edges;  // stored edges of all candidates, summed over the call's passes
 };
 
 // ------------------------------------------------------------------ hashes

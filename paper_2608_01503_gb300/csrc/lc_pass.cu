@@ -620,7 +620,10 @@ __global__ void k_hub_decide(PassArgs a, int first) {
 // neighbour gathers (one 16-byte load each).  The bucket of Section IV-A-1,
 // floor(eps_den * delta / (eps_num * Lambda)), needs a 128-bit division; it
 // is done here, one thread per vertex, off the aggregation kernels.
+// It also sums the candidates' degrees (the afterburner's edge work) into
+// sc->cand_edges for the algorithmic-byte count of the profile.
 __global__ void k_ab_prep(PassArgs a) {
+  long long cand = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
        v += (int64_t)gridDim.x * blockDim.x) {
     AbRec r;
@@ -628,7 +631,9 @@ __global__ void k_ab_prep(PassArgs a) {
     r.D = a.D[v];
     r.q = r.D != kNone ? eps_bucket(a.m, a.gp[graph_of(a, (int32_t)v)].Lam, a.delta[v]) : 0;
     a.ab[v] = r;
+    if (r.D != kNone) cand += a.g.rp[v + 1] - a.g.rp[v];
   }
+  flush_block_sum(cand, &a.sc->cand_edges);
 }
 
 struct AbCtx {

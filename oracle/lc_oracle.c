@@ -929,10 +929,11 @@ static int cmp_tree_item(const void *pa, const void *pb) {
 /* pLeidenR (Algorithm 6) with constraint clustering B: refined labels R
  * (each vertex gets the id of its cluster's tree root, or its own id).
  *   U: vertices with w'(u, B[u] minus u) >= 0 (Lambda-scaled g(u, B[u]) >= 0).
- *   H[v]: for v in U, a uniformly chosen member of the candidate list
- *     [v] followed by the neighbours u in row order with u in U,
- *     B[u] = B[v] and w'(u,v) = w(u,v) - lambda w(u) w(v) >= 0
- *     (value 0 of stream 0, modulo the list length); v itself = no edge.
+ *   H[v]: for v in U, a uniformly chosen candidate among v itself and the
+ *     neighbours u in U with B[u] = B[v] and w'(u,v) = w(u,v) - lambda
+ *     w(u) w(v) >= 0: the one with the smallest (value (v << 32 | c) of
+ *     stream 0, c), so the choice does not depend on the order of the row
+ *     (coarse rows have none); v itself = no edge.
  *   f(v) in [0, K), K = 2^62: value of stream 1, shifted right by 2.
  *   The edge v -> H[v] is kept iff (f(H[v]), H[v]) < (f(v), v).  A vertex
  *   with an edge that is neither kept nor any kept edge's target (a
@@ -968,22 +969,18 @@ static int pleiden_refine(const orc_graph *g, const orc_params *p, const int32_t
   for (int64_t v = 0; v < n; v++) {
     H[v] = v;
     if (!inU[v]) continue;
-    int64_t cnt = 1;
-    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
-      const int64_t u = g->col[e];
-      if (inU[u] && B[u] == B[v] &&
-          (i128)Lam * g->ew[e] - (i128)mu * g->vw[u] * g->vw[v] >= 0)
-        cnt++;
-    }
-    int64_t pick = (int64_t)(orc_rand(p->seed, level, 0, v) % (uint64_t)cnt);
-    if (pick == 0) continue; /* v itself */
+    /* ChooseRandom: the candidate c (v itself or a qualifying neighbour)
+     * with the smallest (rand(v, c), c); uniform over the candidates and
+     * independent of the order of the row. */
+    uint64_t best = orc_rand(p->seed, level, 0, (v << 32) | v);
     for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
       const int64_t u = g->col[e];
       if (inU[u] && B[u] == B[v] &&
           (i128)Lam * g->ew[e] - (i128)mu * g->vw[u] * g->vw[v] >= 0) {
-        if (--pick == 0) {
+        const uint64_t r = orc_rand(p->seed, level, 0, (v << 32) | u);
+        if (r < best || (r == best && u < H[v])) {
+          best = r;
           H[v] = u;
-          break;
         }
       }
     }

@@ -17,8 +17,10 @@
  * The method is Louvain+ (Algorithm 1): coarsening levels of synchronous
  * local-move passes (Algorithm 2) filtered by the afterburner (Algorithm 3),
  * gather-free graph contraction (Algorithm 4), then uncoarsening levels that
- * project and re-run the local-move passes.  All arithmetic is exact integer;
- * results are deterministic and independent of thread scheduling.
+ * project and re-run the local-move passes.  Also: Louvain+ constrained by a
+ * clustering and its iterated form (Section V-B), and pLeiden / pLeiden+
+ * (Section V).  All arithmetic is exact integer; results are deterministic
+ * and independent of thread scheduling.
  *
  * Conventions shared by every entry point:
  *  - Graphs are CSR: row_ptr int64[n+1] (row_ptr[0] = 0, row_ptr[n] = nnz,
@@ -176,6 +178,22 @@ LC_API int lc_cluster(const lc_csr *g, const int64_t *vertex_w, const int32_t *e
 LC_API int lc_cluster_constrained(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
                                   int64_t lambda_num, int64_t lambda_den, const int32_t *constraint,
                                   const lc_opts *opts, int32_t *labels_out, lc_result *res);
+
+/* pLeiden (Algorithm 5, Section V) on G; opts.uncoarsen = 1 (the default)
+ * gives pLeiden+ (LocalMovePasses after each projection), 0 gives pLeiden.
+ * Each level runs LocalMovePasses from its clustering, LocalMoveAlt
+ * (Section V-A) when they leave the objective unchanged, then stops if
+ * every cluster is a singleton, else refines with pLeidenR (Algorithm 6),
+ * contracts on the refinement and starts the coarse level from the
+ * clusters (Downsample).  A refinement that merges nothing also ends the
+ * coarsening.  pLeidenR's random choices come from SplitMix64's output
+ * function on (opts.seed, level, stream, vertex), so runs are reproducible.
+ * initial: device int32[n] starting clustering with labels in [0, n)
+ * (LC_ERR_ARG otherwise), or NULL for singletons.  labels_out and res as
+ * lc_cluster; res.passes_total counts the LocalMovePasses passes. */
+LC_API int lc_cluster_leiden(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
+                             int64_t lambda_num, int64_t lambda_den, const int32_t *initial,
+                             const lc_opts *opts, int32_t *labels_out, lc_result *res);
 
 /* Iterated Louvain+ (Section V-B): `iterations` (>= 1) runs in total; the
  * first is lc_cluster, each further one is lc_cluster_constrained with the

@@ -11,6 +11,7 @@ Functions carry the C names:
   lc_cluster_host   the same on host (numpy) buffers, copies included
   lc_cluster_constrained  Louvain+ with a constraint clustering (Section V-B)
   lc_cluster_iterated     iterated Louvain+ (each run constrained by the last)
+  lc_cluster_leiden       pLeiden / pLeiden+ (Section V)
   lc_local_move     one LocalMovePasses call (Algorithm 2 + Algorithm 3)
   lc_contract       graph contraction (Algorithm 4)
   lc_objective      exact LambdaCC objective (Eq. 1)
@@ -88,7 +89,7 @@ class _ServerConfig(ctypes.Structure):
 
 EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "lc_cluster_host",
            "lc_local_move",
-           "lc_cluster_constrained", "lc_cluster_iterated",
+           "lc_cluster_constrained", "lc_cluster_iterated", "lc_cluster_leiden",
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
            "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
            "lc_server_wait", "lc_server_destroy"]
@@ -120,6 +121,7 @@ def load(build_if_missing: bool = True):
     lib.lc_cluster_host.argtypes = [csr, P, P, i64, i64, opts, P, res]
     lib.lc_cluster_constrained.argtypes = [csr, P, P, i64, i64, P, opts, P, res]
     lib.lc_cluster_iterated.argtypes = [csr, P, P, i64, i64, i32, opts, P, res]
+    lib.lc_cluster_leiden.argtypes = [csr, P, P, i64, i64, P, opts, P, res]
     lib.lc_cluster_batch.argtypes = [csr, P, P, i32, P, P, P, opts, P, res]
     lib.lc_local_move.argtypes = [csr, P, P, i64, i64, opts, P, i32, res]
     lib.lc_contract.argtypes = [csr, P, P, P, i64, opts, P, P, P, P, i64, ctypes.POINTER(i64)]
@@ -305,6 +307,29 @@ def lc_cluster_iterated(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, 
                                  _dev(ew, torch.int32, "ew"), int(lambda_num), int(lambda_den),
                                  int(iterations), ctypes.byref(c),
                                  _dev(labels_out, torch.int32, "labels_out"), ctypes.byref(res))
+    _check(rc, res)
+    return labels_out, _result(res)
+
+
+def lc_cluster_leiden(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, initial=None,
+                      opts: Options | None = None, labels_out=None, stream=None,
+                      trace: Trace | None = None):
+    """pLeiden+ (opts.uncoarsen, the default) or pLeiden on device tensors;
+    `initial`: optional int32 CUDA tensor of starting labels in [0, n).
+    Returns (labels, result)."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    if labels_out is None:
+        labels_out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+    c = _c_opts(opts, _stream_handle(stream), trace.fn if trace else None)
+    res = _Result()
+    init = ctypes.c_void_p(0) if initial is None else _dev(initial, torch.int32, "initial")
+    rc = lib.lc_cluster_leiden(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"),
+                               int(lambda_num), int(lambda_den), init, ctypes.byref(c),
+                               _dev(labels_out, torch.int32, "labels_out"), ctypes.byref(res))
     _check(rc, res)
     return labels_out, _result(res)
 

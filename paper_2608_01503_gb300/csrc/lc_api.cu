@@ -16,6 +16,7 @@
 
 #include "lc_constraint.cuh"
 #include "lc_contract.cuh"
+#include "lc_leiden.cuh"
 #include "lc_internal.cuh"
 #include "lc_pass.cuh"
 #include "lc_scan.cuh"
@@ -889,6 +890,148 @@ static int labels_in_range(Run &r, const int32_t *labels, int64_t n, int64_t lim
   return st2.err_key != ~0ull ? LC_ERR_ARG : LC_OK;
 }
 
+// ----------------------------------------------------------- pLeiden
+
+static int alloc_leiden(Run &r, int64_t n0, LeidenScratch &ls) {
+  LC_TRY(r.ar.get(&ls.list, n0));
+  LC_TRY(r.ar.get(&ls.list2, n0));
+  LC_TRY(r.ar.get(&ls.to, n0));
+  LC_TRY(r.ar.get(&ls.size, n0));
+  LC_TRY(r.ar.get(&ls.H, n0));
+  LC_TRY(r.ar.get(&ls.root, n0));
+  LC_TRY(r.ar.get(&ls.first_bad, n0));
+  LC_TRY(r.ar.get(&ls.pos, n0));
+  LC_TRY(r.ar.get(&ls.f, n0));
+  LC_TRY(r.ar.get(&ls.key, n0));
+  LC_TRY(r.ar.get(&ls.key2, n0));
+  LC_TRY(r.ar.get(&ls.WB, n0));
+  LC_TRY(r.ar.get(&ls.SB, n0));
+  LC_TRY(r.ar.get(&ls.Sv, n0));
+  LC_TRY(r.ar.get(&ls.tv, n0));
+  LC_TRY(r.ar.get(&ls.ps_w, n0));
+  LC_TRY(r.ar.get(&ls.ps_t, n0));
+  LC_TRY(r.ar.get(&ls.flags, n0 + 4));
+  const int64_t hl = radix_hist_len(n0);
+  LC_TRY(r.ar.get(&ls.hist, hl));
+  LC_TRY(r.ar.get(&ls.scan64, scan_scratch(hl > n0 + 1 ? hl : n0 + 1)));
+  LC_TRY(r.ar.get(&ls.scal, 4));
+  return LC_OK;
+}
+
+// pLeiden (Algorithm 5) on one graph; with opts.uncoarsen, pLeiden+.  C0:
+// initial clustering on the device (labels in [0, n)), or null for
+// singletons.  Per level: LocalMovePasses from the level's clustering;
+// LocalMoveAlt when they left Phi unchanged; stop when every cluster is a
+// singleton; otherwise refine (pLeidenR with B = C_l), contract on the
+// refinement and Downsample.  A refinement that merges nothing also ends
+// the coarsening.
+static int pleiden_impl(Run &r, const LevelGraph &g0, const int32_t *C0, int32_t *labels_out) {
+  GraphStats st{};
+  LC_TRY(alloc_per_graph(r));
+  std::vector<Level> lv(1);
+  LC_TRY(level0(r, lv[0], g0, std::vector<int64_t>{0, g0.n}));
+  LC_TRY(prepare(r, g0, nullptr, &st));
+  if (C0) LC_TRY(labels_in_range(r, C0, g0.n, g0.n));  // initial labels must lie in [0, n)
+  LC_TRY(alloc_scratch(r, g0.n, g0.nnz));
+  LeidenScratch ls{};
+  LC_TRY(alloc_leiden(r, g0.n, ls));
+  int32_t *Ccur = nullptr, *Bd = nullptr, *R = nullptr;
+  LC_TRY(r.ar.get(&Ccur, g0.n));
+  LC_TRY(r.ar.get(&Bd, g0.n));
+  LC_TRY(r.ar.get(&R, g0.n));
+  if (C0)
+    LC_CK(cudaMemcpyAsync(Ccur, C0, sizeof(int32_t) * (size_t)g0.n, cudaMemcpyDeviceToDevice, r.s));
+  else
+    launch_iota(Ccur, g0.n, r.s);
+  r.top.assign(1, 0);
+  const std::vector<uint8_t> present{1};
+  int top = 0;
+  for (int l = 0;; ++l) {
+    if (l >= kMaxLevels) return LC_ERR_TIMEOUT;
+    Level &L = lv[l];
+    const int64_t n = L.g.n;
+    LC_TRY(bins_for(r, L));
+    LC_TRY(upload_params(r, L, present));
+    std::vector<long long> phi_in;
+    LC_TRY(objective_of(r, L, Ccur, phi_in));  // leaves the clustering in r.C
+    LC_TRY(local_move_passes(r, L, false, l, 0, present));
+    long long phi_out = 0;
+    LC_CK(cudaMemcpyAsync(&phi_out, r.phi_out, sizeof(long long), cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaStreamSynchronize(r.s));
+    if (phi_out == phi_in[0]) {  // LocalMoveAlt (Section V-A)
+      LC_CK(cudaMemcpyAsync(r.C, r.C_out, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
+      launch_cluster_weights(r.C, L.g.vw, r.W, n, r.s);
+      PassArgs a = pass_args(r, L);
+      a.phi_n = 0;  // candidates: every v with g(v, D[v]) >= g(v, C[v])
+      a.phi_d = 1;
+      launch_pass_begin(r.sc, r.s);
+      r.prof.begin(LC_K_MOVE);
+      r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
+      r.prof.end(12.0 * L.g.nnz + 48.0 * n);
+      r.prof.begin(LC_K_OTHER);
+      launch_local_move_alt(L.g, L.gp, r.C, r.D, r.delta, r.W, ls, &r.sc->error, r.s);
+      r.prof.end(24.0 * n);
+      r.res->kernel_launches[LC_K_OTHER] += 6;
+      LC_CK(cudaMemcpyAsync(r.C_out, r.C, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
+      LC_TRY(launch_check());
+    }
+    std::vector<int64_t> nc;
+    int64_t total = 0;
+    LC_TRY(count_labels(r, L, r.C_out, nc, &total));
+    if (total == n) {  // |C_l| = |V_l|
+      top = l;
+      LC_CK(cudaMemcpyAsync(Ccur, r.C_out, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
+      break;
+    }
+    // B = C_l with dense ids (ascending), its cluster weights, the refinement
+    launch_relabel(r.C_out, r.newid, Bd, n, nullptr, r.gstart, nullptr, 0, r.s);
+    launch_cluster_weights(Bd, L.g.vw, ls.WB, n, r.s);
+    r.prof.begin(LC_K_OTHER);
+    launch_pleiden_refine(L.g, L.gp, Bd, r.o.seed, l, R, ls, &r.sc->error, r.s);
+    r.prof.end(64.0 * L.g.nnz + 200.0 * n);
+    r.res->kernel_launches[LC_K_OTHER] += 40;
+    LC_TRY(launch_check());
+    LC_CK(cudaMemcpyAsync(r.C_out, R, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
+    Level N;
+    bool any = false;
+    LC_TRY(compact_level(r, L, N, l, &any));
+    if (!any) {  // the refinement merged nothing
+      top = l;
+      r.top[0] = l;
+      LC_CK(cudaMemcpyAsync(Ccur, Bd, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
+      break;
+    }
+    lv.push_back(std::move(N));
+    LC_TRY(contract_level(r, lv[l], lv[l + 1], l));
+    launch_downsample(lv[l].Cd, Bd, Ccur, n, r.s);  // coarse vertex x: its members' cluster
+    r.res->kernel_launches[LC_K_OTHER] += 1;
+  }
+  r.res->levels = top + 1;
+  // uncoarsening: project, and for pLeiden+ LocalMovePasses
+  LC_CK(cudaMemcpyAsync(r.C_out, Ccur, sizeof(int32_t) * lv[top].g.n, cudaMemcpyDeviceToDevice, r.s));
+  for (int l = top - 1; l >= 0; --l) {
+    Level &L = lv[l];
+    launch_project(L.Cd, r.C_out, r.C, L.g.n, L.gid, L.gp, lv[l + 1].gp, r.s);
+    r.res->kernel_launches[LC_K_OTHER] += 1;
+    if (r.o.uncoarsen) {
+      LC_TRY(local_move_passes(r, L, false, l, 1, present));
+    } else {
+      LC_CK(cudaMemcpyAsync(r.C_out, r.C, sizeof(int32_t) * L.g.n, cudaMemcpyDeviceToDevice, r.s));
+    }
+  }
+  Level &L0 = lv[0];
+  std::vector<int64_t> nc;
+  int64_t total = 0;
+  LC_TRY(count_labels(r, L0, r.C_out, nc, &total));
+  launch_relabel(r.C_out, r.newid, labels_out, L0.g.n, nullptr, r.gstart, nullptr, 1, r.s);
+  std::vector<long long> phi;
+  LC_TRY(objective_of(r, L0, r.C_out, phi));
+  LC_TRY(check_device_error(r));
+  r.res->n_clusters = nc[0];
+  finish_result(r, 0, r.res, phi[0]);
+  return LC_OK;
+}
+
 }  // namespace lc
 
 // ================================================================ C ABI
@@ -977,6 +1120,28 @@ int lc_cluster_constrained(const lc_csr *g, const int64_t *vertex_w, const int32
   }
   return cluster_single(g, vertex_w, edge_w, lambda_num, lambda_den, constraint, opts, labels_out,
                         res);
+}
+
+int lc_cluster_leiden(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int64_t lambda_num,
+                      int64_t lambda_den, const int32_t *initial, const lc_opts *opts,
+                      int32_t *labels_out, lc_result *res) {
+  if (!res) return LC_ERR_ARG;
+  lc_opts o = resolve_opts(opts);
+  Run r((cudaStream_t)o.stream);
+  int rc = begin_call(r, opts, res, 1);
+  if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
+  if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
+  if (rc == LC_OK && g->n > 0 && !labels_out) rc = LC_ERR_ARG;
+  if (rc == LC_OK && g->n > 0) {
+    r.mu.assign(1, lambda_num);
+    r.Lam.assign(1, lambda_den);
+    LevelGraph g0{g->n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w};
+    rc = pleiden_impl(r, g0, initial, labels_out);
+  } else if (rc == LC_OK) {
+    res->lambda_den = lambda_den;
+  }
+  end_call(r, rc);
+  return rc;
 }
 
 int lc_cluster_iterated(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,

@@ -135,7 +135,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(workload: str, budget_s: float = 20.0):
+def cpu_baseline(workload: str, budget_s: float = 20.0, method: str = "louvain+"):
     """The CPU oracle (single thread, as it stands) on a bounded sample of the
     workload family, reported in the metric's unit."""
     import graphgen as gg
@@ -151,10 +151,15 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     else:
         g = gg.sbm_planted()
         sample = "full Louvain+ on the same SBM graph"
+    if method != "louvain+":
+        sample = sample.replace("Louvain+", {"leiden": "pLeiden", "leiden+": "pLeiden+"}[method])
     runs, t_total = 0, 0.0
     while t_total < budget_s and runs < 5:
         t0 = time.perf_counter()
-        oracle.louvain_plus(g)
+        if method == "louvain+":
+            oracle.louvain_plus(g)
+        else:
+            oracle.pleiden(g, oracle.Params(uncoarsen=method == "leiden+"))
         t_total += time.perf_counter() - t0
         runs += 1
     return {"value": g.nnz * runs / t_total, "unit": "edges/s", "cores": 1, "kind": "oracle",
@@ -454,6 +459,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="graphs of the batched workload")
+    ap.add_argument("--method", default="louvain+", choices=["louvain+", "leiden", "leiden+"],
+                    help="single-graph workloads: Louvain+ (default), pLeiden or pLeiden+")
     ap.add_argument("--iterations", type=int, default=1,
                     help="iterated Louvain+ runs per step (single-graph workloads)")
     ap.add_argument("--requests", type=int, default=2000, help="requests per rate (served)")
@@ -501,7 +508,13 @@ def main():
 
     K = max(1, args.iterations)
 
+    if args.method != "louvain+":  # pLeiden (no uncoarsening) or pLeiden+
+        opts_prof = lc.Options(profile=True, uncoarsen=args.method == "leiden+")
+
     def call():
+        if args.method != "louvain+":
+            return lc.lc_cluster_leiden(rp, col, ew, vw, g.lam_num, g.lam_den, None, opts=opts_prof,
+                                        labels_out=labels)
         if K > 1:  # iterated Louvain+ (Section V-B): K runs, each constrained by the last
             return lc.lc_cluster_iterated(rp, col, ew, vw, g.lam_num, g.lam_den, K, opts=opts_prof,
                                           labels_out=labels)
@@ -544,7 +557,7 @@ def main():
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
-    if not args.no_e2e and K == 1:
+    if not args.no_e2e and K == 1 and args.method == "louvain+":
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         h_rp, h_col, h_ew, h_vw = pin(g.row_ptr), pin(g.col), pin(g.ew), pin(g.vw)
         h_lab = torch.empty(g.n, dtype=torch.int32).pin_memory().numpy()
@@ -577,7 +590,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (hbm_gbs)",
                 "traffic": (TRAFFIC_PER_STEP.get((args.workload, dom))
-                            if args.scale is None and K == 1 else None),
+                            if args.scale is None and K == 1 and args.method == "louvain+" else None),
                 "traffic_unit": "DRAM bytes per step, all launches of the class (ncu)",
                 "launches": klaunch[dom],
                 "algorithmic_bytes_per_step": kbytes[dom] / args.steps}
@@ -593,7 +606,7 @@ def main():
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
                    "n": g.n, "nnz": g.nnz, "edges_counted": "nnz = 2m (both directions), the paper's 2m/t",
                    "l2": "inputs larger than L2 (CSR > 129 MB); no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "method": args.method,
                    **({"iterations": K, "edges_counted_iterated": "nnz once per iteration"}
                       if K > 1 else {})},
         "result": {"n_clusters": res["n_clusters"], "levels": res["levels"],
@@ -607,7 +620,7 @@ def main():
         "gpu_launches": int(sum(klaunch.values())),
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, method=args.method)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

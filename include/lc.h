@@ -130,7 +130,9 @@ enum {
   LC_K_OBJECTIVE = 4,
   LC_K_CONTRACT = 5,   /* label compaction + contraction */
   LC_K_OTHER = 6,      /* binning, projection, validation, guards */
-  LC_K_COUNT = 7
+  LC_K_ALT = 7,        /* pLeiden: LocalMoveAlt (Section V-A) */
+  LC_K_REFINE = 8,     /* pLeiden: pLeidenR refinement (Algorithm 6) */
+  LC_K_COUNT = 9
 };
 
 typedef struct {

@@ -34,7 +34,8 @@ _lib = None
 
 LC_ERR_NOT_READY = 11
 
-LC_K_NAMES = ["first_pass", "move", "afterburner", "apply", "objective", "contract", "other"]
+LC_K_NAMES = ["first_pass", "move", "afterburner", "apply", "objective", "contract", "other",
+              "leiden_alt", "leiden_refine"]
 
 
 class LCError(RuntimeError):
@@ -77,8 +78,8 @@ class _Result(ctypes.Structure):
                 ("passes_total", ctypes.c_int32), ("phi", ctypes.c_int64),
                 ("lambda_den", ctypes.c_int64), ("objective", ctypes.c_double),
                 ("modularity", ctypes.c_double), ("edges_local_move", ctypes.c_int64),
-                ("edges_contract", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 7),
-                ("kernel_launches", ctypes.c_int64 * 7), ("kernel_bytes", ctypes.c_double * 7),
+                ("edges_contract", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 9),
+                ("kernel_launches", ctypes.c_int64 * 9), ("kernel_bytes", ctypes.c_double * 9),
                 ("error_detail", ctypes.c_int64)]
 
 

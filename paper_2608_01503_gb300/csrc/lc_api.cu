@@ -968,10 +968,10 @@ static int pleiden_impl(Run &r, const LevelGraph &g0, const int32_t *C0, int32_t
       r.prof.begin(LC_K_MOVE);
       r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
       r.prof.end(12.0 * L.g.nnz + 48.0 * n);
-      r.prof.begin(LC_K_OTHER);
+      r.prof.begin(LC_K_ALT);
       launch_local_move_alt(L.g, L.gp, r.C, r.D, r.delta, r.W, ls, &r.sc->error, r.s);
       r.prof.end(24.0 * n);
-      r.res->kernel_launches[LC_K_OTHER] += 6;
+      r.res->kernel_launches[LC_K_ALT] += 6;
       LC_CK(cudaMemcpyAsync(r.C_out, r.C, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
       LC_TRY(launch_check());
     }
@@ -986,10 +986,10 @@ static int pleiden_impl(Run &r, const LevelGraph &g0, const int32_t *C0, int32_t
     // B = C_l with dense ids (ascending), its cluster weights, the refinement
     launch_relabel(r.C_out, r.newid, Bd, n, nullptr, r.gstart, nullptr, 0, r.s);
     launch_cluster_weights(Bd, L.g.vw, ls.WB, n, r.s);
-    r.prof.begin(LC_K_OTHER);
-    launch_pleiden_refine(L.g, L.gp, Bd, r.o.seed, l, R, ls, &r.sc->error, r.s);
+    r.prof.begin(LC_K_REFINE);
+    launch_pleiden_refine(L.g, L.bins, L.gp, Bd, r.o.seed, l, R, ls, &r.sc->error, r.s);
     r.prof.end(64.0 * L.g.nnz + 200.0 * n);
-    r.res->kernel_launches[LC_K_OTHER] += 40;
+    r.res->kernel_launches[LC_K_REFINE] += 40;
     LC_TRY(launch_check());
     LC_CK(cudaMemcpyAsync(r.C_out, R, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));
     Level N;

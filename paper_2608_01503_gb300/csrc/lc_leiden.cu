@@ -7,6 +7,7 @@
 
 #include "lc_group.cuh"
 #include "lc_leiden.cuh"
+#include "lc_pass.cuh"
 #include "lc_scan.cuh"
 
 namespace lc {
@@ -152,61 +153,78 @@ __device__ __forceinline__ bool edge_ok(const GraphParam &P, int32_t w, long lon
   return P.Lam * (long long)w - P.mu * wu * wv >= 0;
 }
 
-// Warp per vertex: S(v, B[v]), membership of U, and the key f(v).
+// The per-vertex refinement kernels take the level's degree bins: one
+// thread per vertex up to degree 32 (GS = 1), one warp above (GS = 32).
+
+template <int GS>
+__device__ __forceinline__ long long grp_sum(long long x) {
+  if constexpr (GS == 1) return x;
+  else return warp_sum(x);
+}
+
+// S(v, B[v]), membership of U, and the key f(v).
+template <int GS>
 __global__ void __launch_bounds__(kThreads) k_ref_self(LevelGraph g, const GraphParam *gp,
+                                                       const int32_t *__restrict__ list, int64_t count,
                                                        const int32_t *__restrict__ B,
                                                        const int64_t *__restrict__ WB,
                                                        int64_t *__restrict__ SB, uint8_t *__restrict__ flags,
                                                        uint64_t *__restrict__ f, uint32_t seed,
                                                        int32_t level) {
   const GraphParam P = gp[0];
-  const int lane = threadIdx.x & 31;
-  for (int64_t v = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); v < g.n;
-       v += (int64_t)gridDim.x * kWarps) {
-    const int32_t Bv = B[v];
+  const int r = Grp<GS>::rank();
+  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
+    const int32_t v = active ? list[i] : 0;
+    const int32_t Bv = active ? B[v] : 0;
+    const int64_t beg = active ? g.rp[v] : 0, end = active ? g.rp[v + 1] : 0;
     long long sb = 0;
-    for (int64_t e = g.rp[v] + lane; e < g.rp[v + 1]; e += 32)
+    for (int64_t e = beg + r; e < end; e += GS)
       if (B[__ldg(g.col + e)] == Bv) sb += __ldg(g.ew + e);
-    sb = warp_sum(sb);
-    if (lane == 0) {
+    sb = grp_sum<GS>(sb);
+    if (active && r == 0) {
       const long long wv = g.vw[v];
       SB[v] = sb;
       flags[v] = (P.Lam * sb - P.mu * wv * (WB[Bv] - wv) >= 0) ? kInU : 0;
       f[v] = stream_rand(seed, level, 1, v) >> 2;
     }
-  }
+  });
 }
 
-// Warp per vertex of U: ChooseRandom picks, among v itself and the
-// qualifying neighbours, the candidate c with the smallest (rand(v << 32 |
-// c), c) of stream 0: uniform, and independent of the order of the row.
+// ChooseRandom: among v itself and the qualifying neighbours, the
+// candidate c with the smallest (rand(v << 32 | c), c) of stream 0 --
+// uniform, and independent of the order of the row.
+template <int GS>
 __global__ void __launch_bounds__(kThreads) k_ref_choose(LevelGraph g, const GraphParam *gp,
+                                                         const int32_t *__restrict__ list, int64_t count,
                                                          const int32_t *__restrict__ B,
                                                          const uint8_t *__restrict__ flags,
                                                          int32_t *__restrict__ H, uint32_t seed,
                                                          int32_t level) {
   const GraphParam P = gp[0];
-  const int lane = threadIdx.x & 31;
-  for (int64_t v = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); v < g.n;
-       v += (int64_t)gridDim.x * kWarps) {
+  const int r = Grp<GS>::rank();
+  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
+    const int32_t v = active ? list[i] : 0;
+    const bool inU = active && (flags[v] & kInU);
     uint64_t best = ~0ull;
-    int32_t h = (int32_t)v;
-    if (flags[v] & kInU) {
+    int32_t h = v;
+    if (inU) {
       const int32_t Bv = B[v];
       const long long wv = g.vw[v];
-      best = stream_rand(seed, level, 0, (v << 32) | v);
-      for (int64_t e = g.rp[v] + lane; e < g.rp[v + 1]; e += 32) {
+      best = stream_rand(seed, level, 0, ((int64_t)v << 32) | v);
+      for (int64_t e = g.rp[v] + r; e < g.rp[v + 1]; e += GS) {
         const int32_t u = __ldg(g.col + e);
         if ((flags[u] & kInU) && B[u] == Bv && edge_ok(P, __ldg(g.ew + e), g.vw[u], wv)) {
-          const uint64_t r = stream_rand(seed, level, 0, (v << 32) | u);
-          if (r < best || (r == best && u < h)) {
-            best = r;
+          const uint64_t x = stream_rand(seed, level, 0, ((int64_t)v << 32) | u);
+          if (x < best || (x == best && u < h)) {
+            best = x;
             h = u;
           }
         }
       }
+    }
+    if constexpr (GS > 1) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = GS / 2; o > 0; o >>= 1) {
         const uint64_t ob = __shfl_xor_sync(0xFFFFFFFFu, best, o);
         const int32_t oh = __shfl_xor_sync(0xFFFFFFFFu, h, o);
         if (ob < best || (ob == best && oh < h)) {
@@ -215,8 +233,8 @@ __global__ void __launch_bounds__(kThreads) k_ref_choose(LevelGraph g, const Gra
         }
       }
     }
-    if (lane == 0) H[v] = h;
-  }
+    if (active && r == 0) H[v] = inU ? h : v;
+  });
 }
 
 __global__ void k_ref_keep(const int32_t *__restrict__ H, const uint64_t *__restrict__ f,
@@ -273,28 +291,31 @@ __global__ void k_ref_check_roots(const int32_t *__restrict__ root, int64_t n, i
     if (root[root[v]] != root[v]) *error = 1;
 }
 
-// Warp per vertex: weight to the earlier vertices of its tree (same root,
-// smaller key) and the vertex's term of w(C, B minus C) along the order.
-__global__ void __launch_bounds__(kThreads) k_ref_sv(LevelGraph g, const int32_t *__restrict__ root,
+// Weight to the earlier vertices of the tree (same root, smaller key) and
+// the vertex's term of w(C, B minus C) along the tree order.
+template <int GS>
+__global__ void __launch_bounds__(kThreads) k_ref_sv(LevelGraph g, const int32_t *__restrict__ list,
+                                                     int64_t count, const int32_t *__restrict__ root,
                                                      const uint64_t *__restrict__ f,
                                                      const int64_t *__restrict__ SB,
                                                      int64_t *__restrict__ Sv, int64_t *__restrict__ tv) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t v = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); v < g.n;
-       v += (int64_t)gridDim.x * kWarps) {
-    const int32_t r = root[v];
-    const uint64_t fv = f[v];
+  const int r = Grp<GS>::rank();
+  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
+    const int32_t v = active ? list[i] : 0;
+    const int32_t rv = active ? root[v] : 0;
+    const uint64_t fv = active ? f[v] : 0;
+    const int64_t beg = active ? g.rp[v] : 0, end = active ? g.rp[v + 1] : 0;
     long long s = 0;
-    for (int64_t e = g.rp[v] + lane; e < g.rp[v + 1]; e += 32) {
+    for (int64_t e = beg + r; e < end; e += GS) {
       const int32_t u = __ldg(g.col + e);
-      if (root[u] == r && key_less(f[u], u, fv, v)) s += __ldg(g.ew + e);
+      if (root[u] == rv && key_less(f[u], u, fv, v)) s += __ldg(g.ew + e);
     }
-    s = warp_sum(s);
-    if (lane == 0) {
+    s = grp_sum<GS>(s);
+    if (active && r == 0) {
       Sv[v] = s;
       tv[v] = SB[v] - 2 * s;
     }
-  }
+  });
 }
 
 // ------------------------------------------- LSD radix sort (8-bit digits)
@@ -389,32 +410,54 @@ void radix_sort(uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int64_t n,
   }
 }
 
-__global__ void k_iota_keys(const uint64_t *__restrict__ f, uint64_t *__restrict__ key,
-                            int32_t *__restrict__ val, int64_t n) {
+// Vertices of trees with more than one vertex (every other vertex stays a
+// singleton and takes no part in the sort).
+__global__ void k_mark_trees(const int32_t *__restrict__ root, int32_t *__restrict__ mark, int64_t n) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    key[v] = f[v];
-    val[v] = (int32_t)v;
+    const int32_t r = root[v];
+    if (r != v) {
+      mark[v] = 1;
+      mark[r] = 1;
+    }
   }
 }
+struct MarkIn {
+  const int32_t *mark;
+  __device__ int64_t operator()(int64_t v) const { return mark[v] != 0; }
+};
+struct MarkOut {
+  int32_t *list;
+  __device__ void operator()(int64_t v, int64_t pos, int64_t x) const {
+    if (x) list[pos] = (int32_t)v;
+  }
+};
 
-// After the sort by (f, id): key = root * n + rank of (f, id).
+__global__ void k_tree_sort_keys(const int32_t *__restrict__ list, const uint64_t *__restrict__ f,
+                                 uint64_t *__restrict__ key, const int64_t *m_ptr) {
+  const int64_t m = *m_ptr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    key[i] = f[list[i]];
+}
+
+// After the sort by (f, id): key = root * m + rank of (f, id).
 __global__ void k_tree_keys(const int32_t *__restrict__ order, const int32_t *__restrict__ root,
-                            uint64_t *__restrict__ key, int32_t *__restrict__ val, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+                            uint64_t *__restrict__ key, int32_t *__restrict__ val, int64_t m) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = order[i];
-    key[i] = (uint64_t)root[v] * (uint64_t)n + (uint64_t)i;
+    key[i] = (uint64_t)root[v] * (uint64_t)m + (uint64_t)i;
     val[i] = v;
   }
 }
 
 __global__ void k_positions(const int32_t *__restrict__ order, int64_t *__restrict__ pos,
-                            int32_t *__restrict__ first_bad, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+                            int32_t *__restrict__ first_bad, int64_t m) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     pos[order[i]] = i;
-    first_bad[i] = INT_MAX;
+    first_bad[order[i]] = INT_MAX;  // read only at roots
   }
 }
 
@@ -450,12 +493,13 @@ __global__ void k_ref_test(const int32_t *__restrict__ order, const int32_t *__r
   }
 }
 
-__global__ void k_ref_label(const int32_t *__restrict__ root, const int64_t *__restrict__ pos,
-                            const int32_t *__restrict__ first_bad, int32_t *__restrict__ R, int64_t n) {
+__global__ void k_ref_label(const int32_t *__restrict__ root, const int32_t *__restrict__ mark,
+                            const int64_t *__restrict__ pos, const int32_t *__restrict__ first_bad,
+                            int32_t *__restrict__ R, int64_t n) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = root[v];
-    R[v] = pos[v] < first_bad[r] ? r : (int32_t)v;
+    R[v] = (mark[v] && pos[v] < first_bad[r]) ? r : (int32_t)v;
   }
 }
 
@@ -482,13 +526,18 @@ void launch_local_move_alt(const LevelGraph &g, const GraphParam *gp, int32_t *C
 
 int64_t radix_hist_len(int64_t n) { return 256 * ((n + kRadixTile - 1) / kRadixTile) + 256; }
 
-void launch_pleiden_refine(const LevelGraph &g, const GraphParam *gp, const int32_t *B, uint32_t seed,
-                           int32_t level, int32_t *R, LeidenScratch &ls, int *error, cudaStream_t s) {
+void launch_pleiden_refine(const LevelGraph &g, const Bins &bins, const GraphParam *gp, const int32_t *B,
+                           uint32_t seed, int32_t level, int32_t *R, LeidenScratch &ls, int *error,
+                           cudaStream_t s) {
   const int64_t n = g.n;
   if (n == 0) return;
-  const unsigned gw = ld_grid(n, kWarps), gt = ld_grid(n, 256);
-  k_ref_self<<<gw, kThreads, 0, s>>>(g, gp, B, ls.WB, ls.SB, ls.flags, ls.f, seed, level);
-  k_ref_choose<<<gw, kThreads, 0, s>>>(g, gp, B, ls.flags, ls.H, seed, level);
+  const unsigned gt = ld_grid(n, 256);
+  const BinRange lo = bin_range(bins, 0, 2), hi = bin_range(bins, 3, kBins - 1);
+  const unsigned glo = ld_grid(lo.count, 256), ghi = ld_grid(hi.count, kWarps);
+  if (lo.count) k_ref_self<1><<<glo, kThreads, 0, s>>>(g, gp, lo.list, lo.count, B, ls.WB, ls.SB, ls.flags, ls.f, seed, level);
+  if (hi.count) k_ref_self<32><<<ghi, kThreads, 0, s>>>(g, gp, hi.list, hi.count, B, ls.WB, ls.SB, ls.flags, ls.f, seed, level);
+  if (lo.count) k_ref_choose<1><<<glo, kThreads, 0, s>>>(g, gp, lo.list, lo.count, B, ls.flags, ls.H, seed, level);
+  if (hi.count) k_ref_choose<32><<<ghi, kThreads, 0, s>>>(g, gp, hi.list, hi.count, B, ls.flags, ls.H, seed, level);
   k_ref_keep<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, n);
   k_ref_fix<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, n);
   k_ref_parent<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, ls.root, n);
@@ -496,21 +545,32 @@ void launch_pleiden_refine(const LevelGraph &g, const GraphParam *gp, const int3
   while ((1ll << rounds) < n) ++rounds;
   for (int i = 0; i < rounds; ++i) k_ref_jump<<<gt, 256, 0, s>>>(ls.root, n);
   k_ref_check_roots<<<gt, 256, 0, s>>>(ls.root, n, error);
-  k_ref_sv<<<gw, kThreads, 0, s>>>(g, ls.root, ls.f, ls.SB, ls.Sv, ls.tv);
-  // order by (f, id), then by (root, rank): trees contiguous, keys ascending
-  k_iota_keys<<<gt, 256, 0, s>>>(ls.f, ls.key, ls.list, n);
-  radix_sort(ls.key, ls.list, ls.key2, ls.list2, n, 64, ls.hist, ls.scan64, s);
-  k_tree_keys<<<gt, 256, 0, s>>>(ls.list, ls.root, ls.key2, ls.list2, n);
-  int bits = 1;
-  while (bits < 64 && (((unsigned __int128)1) << bits) < (unsigned __int128)n * (unsigned __int128)n) ++bits;
-  radix_sort(ls.key2, ls.list2, ls.key, ls.list, n, bits, ls.hist, ls.scan64, s);
-  const int32_t *order = ls.list2;
-  k_positions<<<gt, 256, 0, s>>>(order, ls.pos, ls.first_bad, n);
-  scan_apply<int64_t>(n, OrderIn{order, g.vw}, PosOut{ls.ps_w}, ls.scan64, s);
-  scan_apply<int64_t>(n, OrderIn{order, ls.tv}, PosOut{ls.ps_t}, ls.scan64, s);
-  k_ref_test<<<gt, 256, 0, s>>>(order, ls.root, ls.pos, ls.ps_w, ls.ps_t, ls.Sv, g.vw, B, ls.WB, gp,
-                                ls.first_bad, n);
-  k_ref_label<<<gt, 256, 0, s>>>(ls.root, ls.pos, ls.first_bad, R, n);
+  if (lo.count) k_ref_sv<1><<<glo, kThreads, 0, s>>>(g, lo.list, lo.count, ls.root, ls.f, ls.SB, ls.Sv, ls.tv);
+  if (hi.count) k_ref_sv<32><<<ghi, kThreads, 0, s>>>(g, hi.list, hi.count, ls.root, ls.f, ls.SB, ls.Sv, ls.tv);
+  // the vertices of multi-vertex trees, ordered by (f, id) and then by
+  // (root, rank): trees contiguous, keys ascending within each tree
+  cudaMemsetAsync(ls.size, 0, sizeof(int32_t) * (size_t)n, s);
+  k_mark_trees<<<gt, 256, 0, s>>>(ls.root, ls.size, n);
+  scan_apply<int64_t>(n, MarkIn{ls.size}, MarkOut{ls.list}, ls.scan64, s);
+  int64_t m = 0;
+  cudaMemcpyAsync(&m, ls.scan64 + scan_tiles(n), sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (m > 0) {
+    const unsigned gm = ld_grid(m, 256);
+    k_tree_sort_keys<<<gm, 256, 0, s>>>(ls.list, ls.f, ls.key, ls.scan64 + scan_tiles(n));
+    radix_sort(ls.key, ls.list, ls.key2, ls.list2, m, 64, ls.hist, ls.scan64, s);
+    k_tree_keys<<<gm, 256, 0, s>>>(ls.list, ls.root, ls.key2, ls.list2, m);
+    int bits = 1;
+    while (bits < 64 && (((unsigned __int128)1) << bits) < (unsigned __int128)n * (unsigned __int128)m) ++bits;
+    radix_sort(ls.key2, ls.list2, ls.key, ls.list, m, bits, ls.hist, ls.scan64, s);
+    const int32_t *order = ls.list2;
+    k_positions<<<gm, 256, 0, s>>>(order, ls.pos, ls.first_bad, m);
+    scan_apply<int64_t>(m, OrderIn{order, g.vw}, PosOut{ls.ps_w}, ls.scan64, s);
+    scan_apply<int64_t>(m, OrderIn{order, ls.tv}, PosOut{ls.ps_t}, ls.scan64, s);
+    k_ref_test<<<gm, 256, 0, s>>>(order, ls.root, ls.pos, ls.ps_w, ls.ps_t, ls.Sv, g.vw, B, ls.WB, gp,
+                                  ls.first_bad, m);
+  }
+  k_ref_label<<<gt, 256, 0, s>>>(ls.root, ls.size, ls.pos, ls.first_bad, R, n);
 }
 
 void launch_downsample(const int32_t *Cd, const int32_t *C, int32_t *Cc, int64_t n, cudaStream_t s) {

@@ -57,9 +57,12 @@ void launch_local_move_alt(const LevelGraph &g, const GraphParam *gp, int32_t *C
                            const int64_t *delta, int64_t *W, LeidenScratch &ls, int *error,
                            cudaStream_t s);
 // pLeidenR (Algorithm 6) with constraint B (dense labels in [0, n)): refined
-// labels R (tree root ids, or the vertex itself).
-void launch_pleiden_refine(const LevelGraph &g, const GraphParam *gp, const int32_t *B, uint32_t seed,
-                           int32_t level, int32_t *R, LeidenScratch &ls, int *error, cudaStream_t s);
+// labels R (tree root ids, or the vertex itself).  bins: the level's degree
+// bins (per-vertex kernels use a thread up to degree 32, a warp above).
+struct Bins;
+void launch_pleiden_refine(const LevelGraph &g, const Bins &bins, const GraphParam *gp, const int32_t *B,
+                           uint32_t seed, int32_t level, int32_t *R, LeidenScratch &ls, int *error,
+                           cudaStream_t s);
 // Downsample: Cc[Cd[v]] = C[v] for every v (Cc: int32[n_c]).
 void launch_downsample(const int32_t *Cd, const int32_t *C, int32_t *Cc, int64_t n, cudaStream_t s);
 

@@ -76,3 +76,14 @@ def test_served_mix_sampled():
         ref, ores, _ = oracle.louvain_plus(graphs[k])
         assert np.array_equal(labels, ref), graphs[k].name
         assert res["phi"] == ores["phi"], graphs[k].name
+
+
+def test_rmat22_pleiden_whole_run():
+    g = gg.rmat(22, 16, seed=1, wmax=8)
+    labels, res = lc.lc_cluster_leiden(dev(g.row_ptr), dev(g.col), dev(g.ew), dev(g.vw), g.lam_num,
+                                       g.lam_den, None, opts=lc.Options(profile=True, uncoarsen=False))
+    torch.cuda.synchronize()
+    ref, ores, _ = oracle.pleiden(g, oracle.Params(uncoarsen=False))
+    assert np.array_equal(labels.cpu().numpy(), ref)
+    for k in ("phi", "n_clusters", "levels", "passes_total", "modularity"):
+        assert res[k] == ores[k], k

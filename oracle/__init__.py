@@ -54,7 +54,7 @@ class _Params(ctypes.Structure):
                 ("pass_limit", ctypes.c_int32),
                 ("phi_num", ctypes.c_int32 * 16), ("phi_den", ctypes.c_int32 * 16),
                 ("eps_num", ctypes.c_int32), ("eps_den", ctypes.c_int32),
-                ("seed", ctypes.c_uint32), ("uncoarsen", ctypes.c_int32)]
+                ("seed", ctypes.c_uint32), ("uncoarsen", ctypes.c_int32), ("symmetry", ctypes.c_int32)]
 
 
 class _Event(ctypes.Structure):
@@ -132,6 +132,7 @@ class Params:
     eps: tuple = (1, 10)
     seed: int = 0
     uncoarsen: bool = True
+    symmetry: int = 0  # 0 afterburner, 1 none, 2 minimum label heuristic in odd passes
 
 
 def _c_params(lam_num: int, lam_den: int, p: Params) -> _Params:
@@ -144,6 +145,7 @@ def _c_params(lam_num: int, lam_den: int, p: Params) -> _Params:
     cp.eps_num, cp.eps_den = p.eps
     cp.seed = p.seed & 0xFFFFFFFF
     cp.uncoarsen = 1 if p.uncoarsen else 0
+    cp.symmetry = int(p.symmetry)
     return cp
 
 

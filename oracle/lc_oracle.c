@@ -59,6 +59,9 @@ typedef struct {
   int32_t eps_num, eps_den; /* epsilon of the ordering */
   uint32_t seed;            /* salt of the ordering hash */
   int32_t uncoarsen;        /* 1: Louvain+ (Algorithm 1 line 12), 0: Louvain */
+  int32_t symmetry;         /* 0: afterburner filter (Algorithm 3); 1: none, every candidate
+                               moves; 2: minimum label heuristic in odd passes, none in even
+                               ones (the ablations of Section VI) */
 } orc_params;
 
 enum { ORC_EV_PASS = 1, ORC_EV_LMP = 2, ORC_EV_CONTRACT = 3 };
@@ -257,8 +260,9 @@ static int work_alloc(work *w, int64_t n) {
  * u have B[u] = B[v]; Bc[X] holds that common value, ORC_MIXED when the
  * members disagree (such a cluster admits nobody).  Staying and the empty
  * cluster are always allowed. */
-static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, int32_t phi_n,
-                     int32_t phi_d, int32_t *C, work *w, int64_t *count_L, int64_t *count_M) {
+static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, int32_t pass,
+                     int32_t phi_n, int32_t phi_d, int32_t *C, work *w, int64_t *count_L,
+                     int64_t *count_M) {
   const int64_t n = g->n, mu = p->lam_num, Lam = p->lam_den;
   memcpy(w->C_before, C, (size_t)n * sizeof(int32_t));
   cluster_weights(g, C, w->W);
@@ -322,8 +326,28 @@ static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, 
     if (w->in_L[v])
       w->q[v] = (int64_t)floordiv128((i128)p->eps_den * w->delta[v], (i128)p->eps_num * Lam);
 
+  if (p->symmetry != 0) {
+    /* Ablations: no filter, or the minimum label heuristic (a vertex alone
+     * in its cluster may not join another one-vertex cluster with a larger
+     * label, so two singletons never swap) in odd passes. */
+    const int mlh = p->symmetry == 2 && (pass % 2) == 1;
+    int64_t *size = w->acc; /* zero between uses */
+    if (mlh)
+      for (int64_t v = 0; v < n; v++) size[C[v]]++;
+    for (int64_t v = 0; v < n; v++) {
+      if (!w->in_L[v]) continue;
+      const int32_t Cv = C[v], Dv = w->D[v];
+      const int forbid = mlh && size[Cv] == 1 && Dv >= 0 && size[Dv] == 1 && Dv > Cv;
+      w->adj[v] = w->delta[v];
+      w->in_M[v] = !forbid;
+      nM += w->in_M[v];
+    }
+    if (mlh)
+      for (int64_t v = 0; v < n; v++) size[C[v]] = 0;
+  }
+
   /* Algorithm 3: afterburner filter. */
-  for (int64_t v = 0; v < n; v++) {
+  for (int64_t v = 0; v < n && p->symmetry == 0; v++) {
     if (!w->in_L[v]) continue;
     i128 d = w->delta[v];
     const int32_t Cv = C[v], Dv = w->D[v];
@@ -391,7 +415,7 @@ static int local_move_passes(const orc_graph *g, const orc_params *p, const int3
   i128 phi_out = objective(g, p->lam_num, p->lam_den, C, w.W);
   for (int i = 1; i <= p->pass_limit; i++) {
     int64_t nL = 0, nM = 0;
-    one_pass(g, p, B, p->phi_num[i - 1], p->phi_den[i - 1], C, &w, &nL, &nM);
+    one_pass(g, p, B, i, p->phi_num[i - 1], p->phi_den[i - 1], C, &w, &nL, &nM);
     /* one_pass leaves the afterburner arrays intact; W is reused below */
     const i128 phi = objective(g, p->lam_num, p->lam_den, C, w.W);
     if (tr) tr->passes_total++;
@@ -440,7 +464,8 @@ static int local_move_passes(const orc_graph *g, const orc_params *p, const int3
 }
 
 static int check_params(const orc_graph *g, const orc_params *p) {
-  if (!g || !p || g->n < 0 || g->n > 0x7FFFFFFF || p->lam_den <= 0 || p->lam_num < 0 ||
+  if (!g || !p || p->symmetry < 0 || p->symmetry > 2) return ORC_ERR_ARG;
+  if (g->n < 0 || g->n > 0x7FFFFFFF || p->lam_den <= 0 || p->lam_num < 0 ||
       p->lam_num > p->lam_den || p->pass_limit < 0 || p->pass_limit > 16 || p->eps_num <= 0 ||
       p->eps_den <= 0)
     return ORC_ERR_ARG;

@@ -119,6 +119,13 @@ typedef struct {
   void *stream;             /* cudaStream_t */
   lc_event_fn event_cb;     /* optional per-pass / per-level trace (slow: syncs and copies) */
   void *event_ctx;
+  int32_t symmetry;         /* symmetry breaking of the passes: 0 = afterburner filter
+                               (Algorithm 3, default); 1 = none, every candidate moves;
+                               2 = minimum label heuristic in odd passes (a vertex alone in
+                               its cluster may not join another one-vertex cluster with a
+                               larger label), none in even passes.  1 and 2 are the
+                               ablations of Section VI. */
+  int32_t reserved;         /* 0 */
 } lc_opts;
 
 /* Kernel classes timed when opts.profile = 1. */

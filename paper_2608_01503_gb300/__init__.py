@@ -70,7 +70,8 @@ class _Opts(ctypes.Structure):
                 ("eps_den", ctypes.c_int32), ("seed", ctypes.c_uint32),
                 ("uncoarsen", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p)]
+                ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p),
+                ("symmetry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
@@ -163,6 +164,7 @@ class Options:
     uncoarsen: bool = True
     validate: bool = True
     profile: bool = False
+    symmetry: int = 0  # 0 afterburner, 1 none, 2 minimum label heuristic in odd passes
 
 
 def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
@@ -178,6 +180,7 @@ def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     c.uncoarsen = int(bool(o.uncoarsen))
     c.validate = int(bool(o.validate))
     c.profile = int(bool(o.profile))
+    c.symmetry = int(o.symmetry)
     c.stream = stream
     if event_fn is not None:
         c.event_cb = event_fn

@@ -425,7 +425,11 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
       r.prof.end(8.0 * n);
     }
     r.prof.begin(LC_K_AFTERBURNER);
-    r.res->kernel_launches[LC_K_AFTERBURNER] += launch_afterburner(a, L.bins, r.s);
+    if (r.o.symmetry == 0)
+      r.res->kernel_launches[LC_K_AFTERBURNER] += launch_afterburner(a, L.bins, r.s);
+    else  // ablations: no filter, or the minimum label heuristic in odd passes
+      r.res->kernel_launches[LC_K_AFTERBURNER] +=
+          launch_symmetry_ablation(a, r.o.symmetry == 2 && i % 2 == 1, r.cnt, r.s);
     r.prof.end(32.0 * n);  // + 24 B per candidate edge, added from sc->cand_edges at the end
     r.prof.begin(LC_K_APPLY);
     r.res->kernel_launches[LC_K_APPLY] += launch_apply(a, w, r.s);
@@ -630,6 +634,7 @@ static int check_opts(const lc_opts &o) {
   for (int i = 0; i < o.pass_limit; ++i)
     if (o.phi_den[i] <= 0 || o.phi_num[i] < 0 || o.phi_num[i] > o.phi_den[i]) return LC_ERR_ARG;
   if (o.eps_num <= 0 || o.eps_den <= 0) return LC_ERR_ARG;
+  if (o.symmetry < 0 || o.symmetry > 2) return LC_ERR_ARG;
   return LC_OK;
 }
 

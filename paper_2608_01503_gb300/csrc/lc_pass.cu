@@ -1140,6 +1140,41 @@ int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s) {
   return n;
 }
 
+// ------------------------------------- symmetry-breaking ablations
+
+__global__ void k_cluster_sizes(const int32_t *__restrict__ C, int32_t *__restrict__ size, int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&size[C[v]], 1);
+}
+
+// M[v] for every candidate, except (mlh) a vertex alone in its cluster
+// whose destination is another one-vertex cluster with a larger label.
+__global__ void k_symmetry_ablation(PassArgs a, const int32_t *__restrict__ size, int mlh) {
+  long long cntM = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t Dv = a.D[v], Cv = a.C[v];
+    bool keep = Dv != kNone;
+    if (keep && mlh && size[Cv] == 1 && Dv >= 0 && size[Dv] == 1 && Dv > Cv) keep = false;
+    a.M[v] = keep;
+    cntM += keep;
+  }
+  flush_block_sum(cntM, &a.sc->count_M);
+}
+
+int launch_symmetry_ablation(const PassArgs &a, bool mlh, int32_t *size, cudaStream_t s) {
+  if (a.g.n == 0) return 0;
+  int n = 1;
+  if (mlh) {
+    cudaMemsetAsync(size, 0, sizeof(int32_t) * (size_t)a.g.n, s);
+    k_cluster_sizes<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a.C, size, a.g.n);
+    n++;
+  }
+  k_symmetry_ablation<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, size, mlh ? 1 : 0);
+  return n;
+}
+
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
   int n = 0;
   n += launch_vertex_kernel<1>(k_objective<1>, a, bin_range(b, 0, 0), s);

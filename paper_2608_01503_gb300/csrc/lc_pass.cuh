@@ -59,6 +59,10 @@ void launch_pass_begin(Scalars *sc, cudaStream_t s);
 int launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
 int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s);
 int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
+// Ablations of the afterburner: every candidate moves, or (mlh) all but a
+// vertex alone in its cluster whose destination is another one-vertex
+// cluster with a larger label.  size: int32[n] scratch.
+int launch_symmetry_ablation(const PassArgs &a, bool mlh, int32_t *size, cudaStream_t s);
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
 // Scratch of the update step (all [n] of the level).
 struct ApplyScratch {

@@ -36,7 +36,7 @@ def oracle_params(opts):
     if opts is None:
         return oracle.Params()
     return oracle.Params(pass_limit=opts.pass_limit, phi=opts.phi, eps=opts.eps, seed=opts.seed,
-                         uncoarsen=opts.uncoarsen)
+                         uncoarsen=opts.uncoarsen, symmetry=opts.symmetry)
 
 
 def compare_traces(gpu_ev, orc_ev):

@@ -448,6 +448,64 @@ def run_served(args, rank, world):
         dist.destroy_process_group()
 
 
+ABLATIONS = {  # the settings of Section VI's ablation study (Table 2), by name
+    "default": {},
+    "louvain": dict(uncoarsen=False),
+    "louvain_2x_passes": dict(uncoarsen=False, pass_limit=12, phi=[(3, 4)] * 8 + [(1, 4)] * 4),
+    "no_symmetry_phi0": dict(symmetry=1, phi=[(0, 1)] * 6),
+    "phi0": dict(phi=[(0, 1)] * 6),
+    "mlh_phi0": dict(symmetry=2, phi=[(0, 1)] * 6),
+}
+
+
+def run_ablations(args, rank, world):
+    """Each ablation setting timed like the main line on the same graph;
+    slowdown and modularity difference against the default, as in Table 2."""
+    import torch
+
+    import paper_2608_01503_gb300 as lc
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    g = make_graph(args.workload, args.scale)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, col, ew, vw = t(g.row_ptr), t(g.col), t(g.ew), t(g.vw)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    rows, launches = {}, 0
+    for name, kw in ABLATIONS.items():
+        opts = lc.Options(**kw)
+        for _ in range(args.warmup):
+            lc.lc_cluster(rp, col, ew, vw, g.lam_num, g.lam_den, opts=opts, labels_out=labels)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, res = lc.lc_cluster(rp, col, ew, vw, g.lam_num, g.lam_den, opts=opts, labels_out=labels)
+            launches += sum(res["kernel_launches"].values())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        rows[name] = {"ms_per_step": ms, "modularity": res["modularity"], "passes": res["passes_total"],
+                      "levels": res["levels"]}
+    clocks = sampler.stop()
+    base = rows["default"]
+    for r in rows.values():
+        r["slowdown"] = r["ms_per_step"] / base["ms_per_step"]
+        r["modularity_delta"] = r["modularity"] - base["modularity"]
+    line = {"metric": METRIC, "value": g.nnz / (base["ms_per_step"] / 1000.0), "unit": "edges/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
+                       "n": g.n, "nnz": g.nnz, "mode": "ablations (Section VI, Table 2 settings)"},
+            "ablations": rows, "clocks": clocks, "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -459,6 +517,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="graphs of the batched workload")
+    ap.add_argument("--ablations", action="store_true",
+                    help="time the ablation settings of Section VI on the workload's graph")
     ap.add_argument("--method", default="louvain+", choices=["louvain+", "leiden", "leiden+"],
                     help="single-graph workloads: Louvain+ (default), pLeiden or pLeiden+")
     ap.add_argument("--iterations", type=int, default=1,
@@ -483,6 +543,9 @@ def main():
         return
     if args.workload == "served":
         run_served(args, rank, world)
+        return
+    if args.ablations:
+        run_ablations(args, rank, world)
         return
 
     import torch

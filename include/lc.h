@@ -259,7 +259,9 @@ LC_API int lc_server_submit(lc_server *s, const lc_csr *g_host, const int64_t *v
                             int64_t *job_id);
 /* If the job is done: copy its labels (HOST int32[n], may be NULL) and result
  * (may be NULL), report submit-to-done seconds (may be NULL), forget the job
- * and return its status; otherwise LC_ERR_NOT_READY. */
+ * and return its status; otherwise LC_ERR_NOT_READY.  A request that breaks
+ * a precondition or guard fails alone (its admission is re-run job by job)
+ * with that error and res->error_detail; the other jobs are unaffected. */
 LC_API int lc_server_poll(lc_server *s, int64_t job_id, int32_t *labels_out, lc_result *res,
                           double *latency_s);
 /* Like lc_server_poll but blocks until the job is done. */

@@ -77,21 +77,22 @@ void add_offset(T *a, int64_t count, T add, cudaStream_t st) {
   k_add_offset<T><<<(unsigned)b, 256, 0, st>>>(a, count, add);
 }
 
-// Packs the admitted jobs into one CSR on the device (each job copied to its
-// offset, then shifted to global ids) and clusters them in one batched call.
-void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch) {
-  const int count = (int)batch.size();
-  std::vector<int64_t> gptr(count + 1, 0), eptr(count + 1, 0), lam_num(count), lam_den(count);
+// Packs jobs into one CSR on the device (each job copied to its offset,
+// then shifted to global ids) and clusters them in one batched call.
+// labels (host, the packed vertex range) and res[k] are filled on success.
+int cluster_packed(lc_server *s, cudaStream_t st, Job *const *jobs, int count,
+                   std::vector<int32_t> &labels, std::vector<int64_t> &gptr, lc_result *res) {
+  std::vector<int64_t> eptr(count + 1, 0), lam_num(count), lam_den(count);
+  gptr.assign(count + 1, 0);
   for (int k = 0; k < count; ++k) {
-    gptr[k + 1] = gptr[k] + batch[k]->n;
-    eptr[k + 1] = eptr[k] + batch[k]->nnz;
-    lam_num[k] = batch[k]->mu;
-    lam_den[k] = batch[k]->Lam;
+    gptr[k + 1] = gptr[k] + jobs[k]->n;
+    eptr[k + 1] = eptr[k] + jobs[k]->nnz;
+    lam_num[k] = jobs[k]->mu;
+    lam_den[k] = jobs[k]->Lam;
   }
   const int64_t n = gptr[count], nnz = eptr[count];
-  std::vector<int32_t> labels(n > 0 ? n : 1);
+  labels.assign(n > 0 ? n : 1, 0);
   int rc = LC_OK;
-  std::vector<lc_result> res(count);
   int64_t *d_rp = nullptr, *d_vw = nullptr;
   int32_t *d_col = nullptr, *d_ew = nullptr, *d_lab = nullptr;
   if (cudaMallocAsync(&d_rp, 8 * (n + 1), st) != cudaSuccess ||
@@ -104,7 +105,7 @@ void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch) {
   }
   if (rc == LC_OK) {
     for (int k = 0; k < count; ++k) {
-      const Job &j = *batch[k];
+      const Job &j = *jobs[k];
       if (j.n > 0) {
         cudaMemcpyAsync(d_rp + gptr[k], j.rp.data(), 8 * j.n, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(d_vw + gptr[k], j.vw.data(), 8 * j.n, cudaMemcpyHostToDevice, st);
@@ -125,7 +126,7 @@ void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch) {
     if (cudaGetLastError() != cudaSuccess) rc = LC_ERR_CUDA;
     if (rc == LC_OK)
       rc = lc_cluster_batch(&g, d_vw, d_ew, count, gptr.data(), lam_num.data(), lam_den.data(), &o,
-                            d_lab, res.data());
+                            d_lab, res);
     if (rc == LC_OK && n > 0) {
       if (cudaMemcpyAsync(labels.data(), d_lab, 4 * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = LC_ERR_CUDA;
@@ -138,15 +139,37 @@ void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch) {
   if (d_ew) cudaFreeAsync(d_ew, st);
   if (d_lab) cudaFreeAsync(d_lab, st);
   cudaStreamSynchronize(st);
+  return rc;
+}
+
+// Clusters an admission.  If the batched call fails (one request breaks a
+// precondition or a guard), every job is run alone so that only the
+// offending ones report an error.
+void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch) {
+  const int count = (int)batch.size();
+  std::vector<int32_t> labels;
+  std::vector<int64_t> gptr;
+  std::vector<lc_result> res(count);
+  std::vector<int> rcs(count, LC_OK);
+  std::vector<std::vector<int32_t>> own(count);
+  const int rc = cluster_packed(s, st, batch.data(), count, labels, gptr, res.data());
+  if (rc == LC_OK) {
+    for (int k = 0; k < count; ++k) own[k].assign(labels.begin() + gptr[k], labels.begin() + gptr[k + 1]);
+  } else if (count == 1) {
+    rcs[0] = rc;
+  } else {
+    for (int k = 0; k < count; ++k) {
+      rcs[k] = cluster_packed(s, st, &batch[k], 1, labels, gptr, &res[k]);
+      if (rcs[k] == LC_OK) own[k].assign(labels.begin(), labels.begin() + batch[k]->n);
+    }
+  }
   const auto now = Clock::now();
   std::lock_guard<std::mutex> lock(s->mu);
   for (int k = 0; k < count; ++k) {
     Job &j = *batch[k];
-    j.rc = rc;
-    if (rc == LC_OK) {
-      j.labels.assign(labels.begin() + gptr[k], labels.begin() + gptr[k + 1]);
-      j.res = res[k];
-    }
+    j.rc = rcs[k];
+    j.res = res[k];
+    if (rcs[k] == LC_OK) j.labels.swap(own[k]);
     j.state = 2;
     j.t_done = now;
     s->claimed -= j.footprint;
@@ -203,10 +226,8 @@ void worker(lc_server *s) {
 }
 
 int finish_job(lc_server *s, Job &j, int32_t *labels_out, lc_result *res, double *latency_s) {
-  if (j.rc == LC_OK) {
-    if (labels_out && j.n > 0) memcpy(labels_out, j.labels.data(), 4 * (size_t)j.n);
-    if (res) *res = j.res;
-  }
+  if (j.rc == LC_OK && labels_out && j.n > 0) memcpy(labels_out, j.labels.data(), 4 * (size_t)j.n);
+  if (res) *res = j.res;  // on error: zero but for error_detail
   if (latency_s) *latency_s = std::chrono::duration<double>(j.t_done - j.t_submit).count();
   const int rc = j.rc;
   s->jobs.erase(j.id);

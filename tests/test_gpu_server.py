@@ -71,3 +71,29 @@ def test_poll_reports_not_ready_then_result():
     assert got is not None
     ref, ores, _ = oracle.louvain_plus(g)
     assert np.array_equal(got[0], ref) and got[1]["phi"] == ores["phi"]
+
+
+def test_bad_request_fails_alone():
+    """An asymmetric graph and one over the exactness guard, admitted with
+    good requests, fail with their own errors; the others equal the oracle."""
+    good = [gg.rmat(10, seed=k) for k in range(3)]
+    asym = gg.rmat(9, seed=9)
+    ew_bad = asym.ew.copy()
+    ew_bad[0] += 1  # (u,v) and (v,u) now differ
+    heavy = gg.rmat(9, seed=8)
+    ew_heavy = np.full_like(heavy.ew, 2**30)  # sum of edge weights beyond 2^31
+    with lc.Server(slots=1, max_batch=16) as srv:
+        ids = [srv.submit(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den) for g in good[:2]]
+        bad1 = srv.submit(asym.row_ptr, asym.col, ew_bad, asym.vw, asym.lam_num, asym.lam_den)
+        bad2 = srv.submit(heavy.row_ptr, heavy.col, ew_heavy, heavy.vw, 1, 10**12)
+        ids.append(srv.submit(good[2].row_ptr, good[2].col, good[2].ew, good[2].vw, good[2].lam_num,
+                              good[2].lam_den))
+        with pytest.raises(lc.LCError) as e1:
+            srv.wait(bad1)
+        with pytest.raises(lc.LCError) as e2:
+            srv.wait(bad2)
+        outs = [srv.wait(j) for j in ids]
+    assert e1.value.code == 2 and e2.value.code == 6  # asymmetric, overflow
+    for g, (labels, res, _) in zip(good, outs):
+        ref, ores, _ = oracle.louvain_plus(g)
+        assert np.array_equal(labels, ref) and res["phi"] == ores["phi"]

@@ -35,6 +35,14 @@
  * Parity unpinned (readings, no passage fixes them): the hash salt and the
  * bucket rounding of the ordering, and which free ids the empty-cluster
  * movers receive; they are pinned only through GPU/oracle bit-exactness.
+ *
+ * Also here: constrained and iterated Louvain+ (Section V-B), pLeiden and
+ * pLeiden+ (Section V: LocalMoveAlt, pLeidenR, Downsample) and the
+ * symmetry-breaking ablations of Section VI; their pins are in
+ * tests/test_oracle_constrained.py, tests/test_oracle_leiden.py and
+ * tests/test_oracle_ablations.py.  Parity unpinned there: the orientation
+ * of pLeidenR's kept edges (keys falling towards the root) and the order
+ * of LocalMoveAlt's list (ascending ids), which the paper leaves open.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -84,3 +84,12 @@ def test_iterated_rejects_zero_iterations():
     with pytest.raises(lc.LCError):
         lc.lc_cluster_iterated(dev(g.row_ptr), dev(g.col), dev(g.ew), dev(g.vw), g.lam_num,
                                g.lam_den, 0)
+
+
+def test_degenerate_graphs():
+    rp, col, ew = gg.from_edges(2, np.array([0]), np.array([1]))
+    g = gg.modularity_inputs(rp, col, ew)
+    check_constrained(g, np.array([0, 0], dtype=np.int32))
+    check_constrained(g, np.array([0, 1], dtype=np.int32))
+    e = gg.cpm_inputs(np.zeros(5, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), 1, 3)
+    check_constrained(e, np.zeros(4, dtype=np.int32))

@@ -69,3 +69,24 @@ def test_rejects_initial_labels_out_of_range():
     with pytest.raises(lc.LCError):
         lc.lc_cluster_leiden(dev(g.row_ptr), dev(g.col), dev(g.ew), dev(g.vw), g.lam_num, g.lam_den,
                              dev(bad))
+
+
+@pytest.mark.parametrize("plus", [False, True])
+def test_degenerate_graphs(plus):
+    """Single vertex, edgeless graph, one edge, a star."""
+    cases = [gg.cpm_inputs(np.zeros(2, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), 1, 2),
+             gg.cpm_inputs(np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), 1, 2)]
+    rp, col, ew = gg.from_edges(2, np.array([0]), np.array([1]))
+    cases.append(gg.modularity_inputs(rp, col, ew))
+    rp, col, ew = gg.from_edges(40, np.zeros(39, np.int64), np.arange(1, 40))
+    cases.append(gg.modularity_inputs(rp, col, ew))
+    for g in cases:
+        check_leiden(g, plus)
+
+
+def test_empty_graph():
+    g = gg.cpm_inputs(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), 1, 2)
+    labels, res = lc.lc_cluster_leiden(dev(g.row_ptr), torch.zeros(0, dtype=torch.int32, device="cuda"),
+                                       torch.zeros(0, dtype=torch.int32, device="cuda"),
+                                       torch.zeros(0, dtype=torch.int64, device="cuda"), 1, 2)
+    assert labels.numel() == 0 and res["n_clusters"] == 0

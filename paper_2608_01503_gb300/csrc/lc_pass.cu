@@ -472,9 +472,24 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
     split_argmax<GS>(a, P, tab, cap, wv, threadIdx.x, gb, xb);
-    Grp<GS>::argmax(gb, xb, rg, rx);
-    self = Grp<GS>::sum(self, rs);
+    // one reduction of (best gain, cluster, S_self) for thread 0 only: warp
+    // level, one barrier, thread 0 combines the warps
+    group_argmax<32>(gb, xb);
+    self = warp_sum(self);
+    if ((threadIdx.x & 31) == 0) {
+      rg[threadIdx.x >> 5] = gb;
+      rx[threadIdx.x >> 5] = xb;
+      rs[threadIdx.x >> 5] = self;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      for (int w = 1; w < GS / 32; ++w) {
+        self += rs[w];
+        if (better(rg[w], rx[w], gb, xb)) {
+          gb = rg[w];
+          xb = rx[w];
+        }
+      }
       const long long gC = gain_self(P, self, wv, WC);
       add_self(a, v, gC, phi);
       decide(a, P, v, gC, xb, gb, cntL);

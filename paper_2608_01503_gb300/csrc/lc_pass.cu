@@ -737,24 +737,53 @@ template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 4)
     k_afterburner(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
   constexpr int U = 4;
-  __shared__ long long rs[GS > 32 ? GS / 32 : 1];
   long long cntM = 0;
   const int r = Grp<GS>::rank();
-  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
-    const int32_t v = active ? list[i] : 0;
-    const int32_t Dv = active ? a.D[v] : kNone;
-    long long acc = 0;
-    if (Dv != kNone) {
+  if constexpr (GS > 32) {
+    // block per vertex: non-candidates are skipped by the whole block, and
+    // the per-warp sums alternate between two buffers, so one barrier per
+    // candidate suffices (the next candidate's barrier orders thread 0's
+    // reads before the buffer is written again)
+    __shared__ long long rs[2][GS / 32];
+    int par = 0;
+    for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+      const int32_t v = list[i];
+      const int32_t Dv = a.D[v];
+      if (Dv == kNone) {
+        if (threadIdx.x == 0) a.M[v] = 0;
+        continue;
+      }
       const AbCtx c = ab_ctx(a, v);
-      acc = ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r);
+      long long acc = warp_sum(ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r));
+      if ((threadIdx.x & 31) == 0) rs[par][threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < GS / 32; ++w) t += rs[par][w];
+        const bool keep = a.delta[v] + t >= 0;
+        a.M[v] = keep;
+        cntM += keep;
+      }
+      par ^= 1;
     }
-    acc = Grp<GS>::sum(acc, rs);
-    if (active && r == 0) {
-      const bool keep = Dv != kNone && a.delta[v] + acc >= 0;
-      a.M[v] = keep;
-      cntM += keep;
-    }
-  });
+  } else {
+    __shared__ long long rs[1];
+    for_each_vertex<GS>(count, [&](int64_t i, bool active) {
+      const int32_t v = active ? list[i] : 0;
+      const int32_t Dv = active ? a.D[v] : kNone;
+      long long acc = 0;
+      if (Dv != kNone) {
+        const AbCtx c = ab_ctx(a, v);
+        acc = ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r);
+      }
+      acc = Grp<GS>::sum(acc, rs);
+      if (active && r == 0) {
+        const bool keep = Dv != kNone && a.delta[v] + acc >= 0;
+        a.M[v] = keep;
+        cntM += keep;
+      }
+    });
+  }
   flush_block_sum(cntM, &a.sc->count_M);
 }
 

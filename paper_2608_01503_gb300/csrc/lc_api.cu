@@ -920,6 +920,8 @@ static int alloc_leiden(Run &r, int64_t n0, LeidenScratch &ls) {
   LC_TRY(r.ar.get(&ls.hist, hl));
   LC_TRY(r.ar.get(&ls.scan64, scan_scratch(hl > n0 + 1 ? hl : n0 + 1)));
   LC_TRY(r.ar.get(&ls.scal, 4));
+  LC_TRY(r.ar.get(&ls.rec, n0));
+  LC_TRY(r.ar.get(&ls.krec, n0));
   return LC_OK;
 }
 

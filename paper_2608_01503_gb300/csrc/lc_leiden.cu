@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(kThreads) k_ref_self(LevelGraph g, const Graph
                                                        const int32_t *__restrict__ B,
                                                        const int64_t *__restrict__ WB,
                                                        int64_t *__restrict__ SB, uint8_t *__restrict__ flags,
-                                                       uint64_t *__restrict__ f, uint32_t seed,
-                                                       int32_t level) {
+                                                       uint64_t *__restrict__ f, RefRec *__restrict__ rec,
+                                                       uint32_t seed, int32_t level) {
   const GraphParam P = gp[0];
   const int r = Grp<GS>::rank();
   for_each_vertex<GS>(count, [&](int64_t i, bool active) {
@@ -183,9 +183,11 @@ __global__ void __launch_bounds__(kThreads) k_ref_self(LevelGraph g, const Graph
     sb = grp_sum<GS>(sb);
     if (active && r == 0) {
       const long long wv = g.vw[v];
+      const bool inU = P.Lam * sb - P.mu * wv * (WB[Bv] - wv) >= 0;
       SB[v] = sb;
-      flags[v] = (P.Lam * sb - P.mu * wv * (WB[Bv] - wv) >= 0) ? kInU : 0;
+      flags[v] = inU ? kInU : 0;
       f[v] = stream_rand(seed, level, 1, v) >> 2;
+      rec[v] = RefRec{Bv, inU ? 1 : 0, wv};
     }
   });
 }
@@ -196,24 +198,23 @@ __global__ void __launch_bounds__(kThreads) k_ref_self(LevelGraph g, const Graph
 template <int GS>
 __global__ void __launch_bounds__(kThreads) k_ref_choose(LevelGraph g, const GraphParam *gp,
                                                          const int32_t *__restrict__ list, int64_t count,
-                                                         const int32_t *__restrict__ B,
-                                                         const uint8_t *__restrict__ flags,
+                                                         const RefRec *__restrict__ rec,
                                                          int32_t *__restrict__ H, uint32_t seed,
                                                          int32_t level) {
   const GraphParam P = gp[0];
   const int r = Grp<GS>::rank();
   for_each_vertex<GS>(count, [&](int64_t i, bool active) {
     const int32_t v = active ? list[i] : 0;
-    const bool inU = active && (flags[v] & kInU);
+    const RefRec rv = active ? rec[v] : RefRec{0, 0, 0};
+    const bool inU = active && rv.inU;
     uint64_t best = ~0ull;
     int32_t h = v;
     if (inU) {
-      const int32_t Bv = B[v];
-      const long long wv = g.vw[v];
       best = stream_rand(seed, level, 0, ((int64_t)v << 32) | v);
       for (int64_t e = g.rp[v] + r; e < g.rp[v + 1]; e += GS) {
         const int32_t u = __ldg(g.col + e);
-        if ((flags[u] & kInU) && B[u] == Bv && edge_ok(P, __ldg(g.ew + e), g.vw[u], wv)) {
+        const RefRec ru = rec[u];  // one gather: B[u], u in U, w(u)
+        if (ru.inU && ru.B == rv.B && edge_ok(P, __ldg(g.ew + e), ru.w, rv.w)) {
           const uint64_t x = stream_rand(seed, level, 0, ((int64_t)v << 32) | u);
           if (x < best || (x == best && u < h)) {
             best = x;
@@ -277,38 +278,53 @@ __global__ void k_ref_parent(const int32_t *__restrict__ H, const uint64_t *__re
   }
 }
 
-// Pointer jumping (keys strictly decrease towards the root, so the trees
-// have no cycles; ceil(log2 n) rounds reach every root).
-__global__ void k_ref_jump(int32_t *__restrict__ root, int64_t n) {
+// Roots by following parents (keys strictly decrease towards the root, so
+// there are no cycles; with random keys a tree has logarithmic expected
+// depth).  parent and root are separate arrays; a walk longer than n sets
+// the error flag.
+__global__ void k_ref_roots(const int32_t *__restrict__ parent, int32_t *__restrict__ root, int64_t n,
+                            int *error) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    root[v] = root[root[v]];
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = (int32_t)v;
+    int64_t steps = 0;
+    for (int32_t p = parent[r]; p != r && steps <= n; p = parent[r]) {
+      r = p;
+      ++steps;
+    }
+    if (steps > n) *error = 1;
+    root[v] = r;
+  }
 }
 
-__global__ void k_ref_check_roots(const int32_t *__restrict__ root, int64_t n, int *error) {
+// Checks that every root is final and packs (root, key) per vertex.
+__global__ void k_ref_check_roots(const int32_t *__restrict__ root, const uint64_t *__restrict__ f,
+                                  KeyRec *__restrict__ krec, int64_t n, int *error) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    if (root[root[v]] != root[v]) *error = 1;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = root[v];
+    if (root[r] != r) *error = 1;
+    krec[v] = KeyRec{r, 0, f[v]};
+  }
 }
 
 // Weight to the earlier vertices of the tree (same root, smaller key) and
 // the vertex's term of w(C, B minus C) along the tree order.
 template <int GS>
 __global__ void __launch_bounds__(kThreads) k_ref_sv(LevelGraph g, const int32_t *__restrict__ list,
-                                                     int64_t count, const int32_t *__restrict__ root,
-                                                     const uint64_t *__restrict__ f,
+                                                     int64_t count, const KeyRec *__restrict__ krec,
                                                      const int64_t *__restrict__ SB,
                                                      int64_t *__restrict__ Sv, int64_t *__restrict__ tv) {
   const int r = Grp<GS>::rank();
   for_each_vertex<GS>(count, [&](int64_t i, bool active) {
     const int32_t v = active ? list[i] : 0;
-    const int32_t rv = active ? root[v] : 0;
-    const uint64_t fv = active ? f[v] : 0;
+    const KeyRec kv = active ? krec[v] : KeyRec{0, 0, 0};
     const int64_t beg = active ? g.rp[v] : 0, end = active ? g.rp[v + 1] : 0;
     long long s = 0;
     for (int64_t e = beg + r; e < end; e += GS) {
       const int32_t u = __ldg(g.col + e);
-      if (root[u] == rv && key_less(f[u], u, fv, v)) s += __ldg(g.ew + e);
+      const KeyRec ku = krec[u];  // one gather: root and key of u
+      if (ku.root == kv.root && key_less(ku.f, u, kv.f, v)) s += __ldg(g.ew + e);
     }
     s = grp_sum<GS>(s);
     if (active && r == 0) {
@@ -534,19 +550,17 @@ void launch_pleiden_refine(const LevelGraph &g, const Bins &bins, const GraphPar
   const unsigned gt = ld_grid(n, 256);
   const BinRange lo = bin_range(bins, 0, 2), hi = bin_range(bins, 3, kBins - 1);
   const unsigned glo = ld_grid(lo.count, 256), ghi = ld_grid(hi.count, kWarps);
-  if (lo.count) k_ref_self<1><<<glo, kThreads, 0, s>>>(g, gp, lo.list, lo.count, B, ls.WB, ls.SB, ls.flags, ls.f, seed, level);
-  if (hi.count) k_ref_self<32><<<ghi, kThreads, 0, s>>>(g, gp, hi.list, hi.count, B, ls.WB, ls.SB, ls.flags, ls.f, seed, level);
-  if (lo.count) k_ref_choose<1><<<glo, kThreads, 0, s>>>(g, gp, lo.list, lo.count, B, ls.flags, ls.H, seed, level);
-  if (hi.count) k_ref_choose<32><<<ghi, kThreads, 0, s>>>(g, gp, hi.list, hi.count, B, ls.flags, ls.H, seed, level);
+  if (lo.count) k_ref_self<1><<<glo, kThreads, 0, s>>>(g, gp, lo.list, lo.count, B, ls.WB, ls.SB, ls.flags, ls.f, ls.rec, seed, level);
+  if (hi.count) k_ref_self<32><<<ghi, kThreads, 0, s>>>(g, gp, hi.list, hi.count, B, ls.WB, ls.SB, ls.flags, ls.f, ls.rec, seed, level);
+  if (lo.count) k_ref_choose<1><<<glo, kThreads, 0, s>>>(g, gp, lo.list, lo.count, ls.rec, ls.H, seed, level);
+  if (hi.count) k_ref_choose<32><<<ghi, kThreads, 0, s>>>(g, gp, hi.list, hi.count, ls.rec, ls.H, seed, level);
   k_ref_keep<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, n);
   k_ref_fix<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, n);
-  k_ref_parent<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, ls.root, n);
-  int rounds = 1;
-  while ((1ll << rounds) < n) ++rounds;
-  for (int i = 0; i < rounds; ++i) k_ref_jump<<<gt, 256, 0, s>>>(ls.root, n);
-  k_ref_check_roots<<<gt, 256, 0, s>>>(ls.root, n, error);
-  if (lo.count) k_ref_sv<1><<<glo, kThreads, 0, s>>>(g, lo.list, lo.count, ls.root, ls.f, ls.SB, ls.Sv, ls.tv);
-  if (hi.count) k_ref_sv<32><<<ghi, kThreads, 0, s>>>(g, hi.list, hi.count, ls.root, ls.f, ls.SB, ls.Sv, ls.tv);
+  k_ref_parent<<<gt, 256, 0, s>>>(ls.H, ls.f, ls.flags, ls.first_bad, n);  // parents
+  k_ref_roots<<<gt, 256, 0, s>>>(ls.first_bad, ls.root, n, error);
+  k_ref_check_roots<<<gt, 256, 0, s>>>(ls.root, ls.f, ls.krec, n, error);
+  if (lo.count) k_ref_sv<1><<<glo, kThreads, 0, s>>>(g, lo.list, lo.count, ls.krec, ls.SB, ls.Sv, ls.tv);
+  if (hi.count) k_ref_sv<32><<<ghi, kThreads, 0, s>>>(g, hi.list, hi.count, ls.krec, ls.SB, ls.Sv, ls.tv);
   // the vertices of multi-vertex trees, ordered by (f, id) and then by
   // (root, rank): trees contiguous, keys ascending within each tree
   cudaMemsetAsync(ls.size, 0, sizeof(int32_t) * (size_t)n, s);

@@ -22,6 +22,18 @@ __host__ __device__ inline uint64_t stream_rand(uint32_t seed, int32_t level, in
   return sm64_mix(key + (uint64_t)(c + 1) * 0x9E3779B97F4A7C15ull);
 }
 
+// Per-vertex records gathered once per edge by pLeidenR's row sweeps.
+struct __align__(16) RefRec {  // constraint label, membership of U, w(v)
+  int32_t B;
+  int32_t inU;
+  long long w;
+};
+struct __align__(16) KeyRec {  // tree root and ordering key
+  int32_t root;
+  int32_t pad;
+  uint64_t f;
+};
+
 // Scratch of LocalMoveAlt and pLeidenR (n = vertices of the level).
 struct LeidenScratch {
   int32_t *list;        // [n] non-node-optimal vertices / sort values
@@ -45,6 +57,8 @@ struct LeidenScratch {
   int64_t *scan64;      // scan scratch: scan_scratch(max(n, radix_hist_len(n)))
   int32_t *hist;        // radix histograms: radix_hist_len(n)
   int64_t *scal;        // [4] device scalars: m, committed, error
+  RefRec *rec;          // [n]
+  KeyRec *krec;         // [n]
 };
 
 // Elements of hist / scan64 the radix sort of n keys needs.

@@ -167,36 +167,58 @@ def cpu_baseline(workload: str, budget_s: float = 20.0, method: str = "louvain+"
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle timed as it stands on the host cores."""
+    """--impl reference: the CPU oracle timed as it stands on the host cores,
+    one bounded sample of the workload per step, in the metric's unit."""
     if rank != 0:
         return
     import graphgen as gg
     import oracle
 
-    if args.workload == "rmat22":
-        g = gg.rmat(17, 16, seed=1, wmax=8)
+    unit = "edges/s"
+    if args.workload == "batched":
+        graphs = gg.batched_sbms(args.count, seed=3, indices=list(range(0, args.count, 64)))
+        sample = f"every 64th graph of the batched workload ({len(graphs)} graphs), one oracle call each"
+        unit = "graphs/s"
+    elif args.workload == "served":
+        graphs = gg.served_requests(8, seed=4)
+        sample = "the first 8 requests of the served stream, one oracle call each"
+        unit = "graphs/s"
+    elif args.workload == "rmat22":
+        graphs = [gg.rmat(17, 16, seed=1, wmax=8)]
         sample = "R-MAT scale 17 sample of the workload (same recipe)"
     elif args.workload == "grid256":
-        g = gg.grid_cpm(side=48)
+        graphs = [gg.grid_cpm(side=48)]
         sample = "48^3 grid sample of the workload (same recipe)"
     else:
-        g = gg.sbm_planted()
+        graphs = [gg.sbm_planted()]
         sample = "the SBM graph itself"
+    method = getattr(args, "method", "louvain+")
+    if method != "louvain+":
+        sample += f"; {'pLeiden+' if method == 'leiden+' else 'pLeiden'}"
+
+    def one_step():
+        for g in graphs:
+            if method == "louvain+":
+                oracle.louvain_plus(g)
+            else:
+                oracle.pleiden(g, oracle.Params(uncoarsen=method == "leiden+"))
+
     for _ in range(args.warmup):
-        oracle.louvain_plus(g)
+        one_step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.louvain_plus(g)
+        one_step()
     dt = time.perf_counter() - t0
-    value = g.nnz * args.steps / dt
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+    per_step = len(graphs) if unit == "graphs/s" else sum(g.nnz for g in graphs)
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
-                       "sample": sample, "nnz": g.nnz},
-            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                       "sample": sample, "nnz": sum(g.nnz for g in graphs)},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 

@@ -126,6 +126,9 @@ typedef struct {
                                larger label), none in even passes.  1 and 2 are the
                                ablations of Section VI. */
   int32_t reserved;         /* 0 */
+  int64_t scratch_limit;    /* bytes of device scratch one call may hold at once; 0 = no
+                               limit.  A call that needs more returns LC_ERR_OOM (nothing
+                               is kept allocated), as when the device itself runs out. */
 } lc_opts;
 
 /* Kernel classes timed when opts.profile = 1. */
@@ -267,6 +270,10 @@ LC_API int lc_server_poll(lc_server *s, int64_t job_id, int32_t *labels_out, lc_
 /* Like lc_server_poll but blocks until the job is done. */
 LC_API int lc_server_wait(lc_server *s, int64_t job_id, int32_t *labels_out, lc_result *res,
                           double *latency_s);
+/* Withdraws a job that is still queued: LC_OK (the id is then unknown),
+ * LC_ERR_NOT_READY if it is already running or done (poll or wait for it),
+ * LC_ERR_ARG for an unknown id. */
+LC_API int lc_server_cancel(lc_server *s, int64_t job_id);
 /* Finishes the queued and running jobs, stops the workers, frees the server. */
 LC_API int lc_server_destroy(lc_server *s);
 

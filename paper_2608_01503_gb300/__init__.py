@@ -71,7 +71,8 @@ class _Opts(ctypes.Structure):
                 ("uncoarsen", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p),
-                ("symmetry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("symmetry", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("scratch_limit", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):
@@ -94,7 +95,7 @@ EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "
            "lc_cluster_constrained", "lc_cluster_iterated", "lc_cluster_leiden",
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
            "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
-           "lc_server_wait", "lc_server_destroy"]
+           "lc_server_wait", "lc_server_destroy", "lc_server_cancel"]
 
 
 def library_path() -> str:
@@ -139,8 +140,9 @@ def load(build_if_missing: bool = True):
     lib.lc_server_poll.argtypes = [srv, i64, P, res, ctypes.POINTER(ctypes.c_double)]
     lib.lc_server_wait.argtypes = [srv, i64, P, res, ctypes.POINTER(ctypes.c_double)]
     lib.lc_server_destroy.argtypes = [srv]
+    lib.lc_server_cancel.argtypes = [srv, i64]
     for f in ("lc_server_create", "lc_server_submit", "lc_server_poll", "lc_server_wait",
-              "lc_server_destroy"):
+              "lc_server_destroy", "lc_server_cancel"):
         getattr(lib, f).restype = ctypes.c_int
     for f in ("lc_cluster", "lc_cluster_batch", "lc_cluster_host", "lc_local_move", "lc_contract",
               "lc_objective", "lc_objective_static"):
@@ -165,6 +167,7 @@ class Options:
     validate: bool = True
     profile: bool = False
     symmetry: int = 0  # 0 afterburner, 1 none, 2 minimum label heuristic in odd passes
+    scratch_limit: int = 0  # bytes of device scratch a call may hold; 0 = no limit
 
 
 def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
@@ -181,6 +184,7 @@ def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     c.validate = int(bool(o.validate))
     c.profile = int(bool(o.profile))
     c.symmetry = int(o.symmetry)
+    c.scratch_limit = int(o.scratch_limit)
     c.stream = stream
     if event_fn is not None:
         c.event_cb = event_fn
@@ -524,6 +528,16 @@ def lc_server_wait(server, jid: int, n: int):
     return _server_take(load().lc_server_wait, server, jid, n)
 
 
+def lc_server_cancel(server, jid: int) -> bool:
+    """Withdraws a queued job: True if it was withdrawn, False if it already
+    runs or is done."""
+    rc = load().lc_server_cancel(server, jid)
+    if rc == LC_ERR_NOT_READY:
+        return False
+    _check(rc)
+    return True
+
+
 def lc_server_destroy(server) -> None:
     _check(load().lc_server_destroy(server))
 
@@ -552,6 +566,12 @@ class Server:
         got = lc_server_wait(self._h, jid, self._n[jid])
         del self._n[jid]
         return got
+
+    def cancel(self, jid: int) -> bool:
+        done = lc_server_cancel(self._h, jid)
+        if done:
+            del self._n[jid]
+        return done
 
     def close(self):
         if self._h:

@@ -57,6 +57,8 @@ static int launch_check() {
 struct Arena {
   cudaStream_t s;
   std::vector<void *> ptrs;
+  std::vector<size_t> sizes;
+  int64_t limit = 0, held = 0;  // opts.scratch_limit (0 = none) and bytes held
   explicit Arena(cudaStream_t st) : s(st) {}
   Arena(const Arena &) = delete;
   ~Arena() {
@@ -66,6 +68,10 @@ struct Arena {
   int get(T **out, int64_t count) {
     void *p = nullptr;
     const size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    if (limit > 0 && held + (int64_t)bytes > limit) {
+      *out = nullptr;
+      return LC_ERR_OOM;
+    }
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -73,14 +79,17 @@ struct Arena {
       return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
     }
     ptrs.push_back(p);
+    sizes.push_back(bytes);
+    held += (int64_t)bytes;
     *out = (T *)p;
     return LC_OK;
   }
   void release(void *p) {
-    for (auto &q : ptrs)
-      if (q == p) {
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i] == p) {
         cudaFreeAsync(p, s);
-        q = nullptr;
+        ptrs[i] = nullptr;
+        held -= (int64_t)sizes[i];
       }
   }
 };
@@ -635,6 +644,7 @@ static int check_opts(const lc_opts &o) {
     if (o.phi_den[i] <= 0 || o.phi_num[i] < 0 || o.phi_num[i] > o.phi_den[i]) return LC_ERR_ARG;
   if (o.eps_num <= 0 || o.eps_den <= 0) return LC_ERR_ARG;
   if (o.symmetry < 0 || o.symmetry > 2) return LC_ERR_ARG;
+  if (o.scratch_limit < 0) return LC_ERR_ARG;
   return LC_OK;
 }
 
@@ -850,6 +860,7 @@ static int begin_call(Run &r, const lc_opts *opts, lc_result *res, int G) {
   r.G = G;
   memset(res, 0, sizeof(lc_result) * (size_t)G);
   LC_TRY(check_opts(r.o));
+  r.ar.limit = r.o.scratch_limit;
   keep_pool_memory();
   r.prof.on = r.o.profile != 0;
   r.prof.s = r.s;

@@ -332,6 +332,22 @@ LC_API int lc_server_wait(lc_server *s, int64_t job_id, int32_t *labels_out, lc_
   }
 }
 
+LC_API int lc_server_cancel(lc_server *s, int64_t job_id) {
+  if (!s) return LC_ERR_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return LC_ERR_ARG;
+  if (it->second.state != 0) return LC_ERR_NOT_READY;
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if (*q == job_id) {
+      s->queue.erase(q);
+      break;
+    }
+  s->jobs.erase(it);
+  s->cv_work.notify_all();  // the head of the queue may have changed
+  return LC_OK;
+}
+
 LC_API int lc_server_destroy(lc_server *s) {
   if (!s) return LC_ERR_ARG;
   {

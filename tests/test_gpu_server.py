@@ -97,3 +97,34 @@ def test_bad_request_fails_alone():
     for g, (labels, res, _) in zip(good, outs):
         ref, ores, _ = oracle.louvain_plus(g)
         assert np.array_equal(labels, ref) and res["phi"] == ores["phi"]
+
+
+def test_cancel_a_queued_request():
+    """With a 1-byte budget jobs run one at a time, so requests submitted
+    while a large one runs stay queued and can be withdrawn."""
+    big = gg.rmat(17, seed=1)
+    small = [gg.rmat(9, seed=k) for k in range(3)]
+    with lc.Server(slots=1, hbm_budget=1) as srv:
+        jb = srv.submit(big.row_ptr, big.col, big.ew, big.vw, big.lam_num, big.lam_den)
+        js = [srv.submit(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den) for g in small]
+        assert srv.cancel(js[1]) is True
+        with pytest.raises(lc.LCError):
+            lc.lc_server_wait(srv._h, js[1], 10)  # the id is gone
+        out = {j: srv.wait(j) for j in (jb, js[0], js[2])}
+    for g, j in ((big, jb), (small[0], js[0]), (small[2], js[2])):
+        ref, ores, _ = oracle.louvain_plus(g)
+        assert np.array_equal(out[j][0], ref) and out[j][1]["phi"] == ores["phi"]
+
+
+def test_scratch_limit_gives_oom_and_leaves_no_state():
+    g = gg.rmat(14, seed=2)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (t(g.row_ptr), t(g.col), t(g.ew), t(g.vw), g.lam_num, g.lam_den)
+    with pytest.raises(lc.LCError) as e:
+        lc.lc_cluster(*args, opts=lc.Options(scratch_limit=1 << 20))
+    assert e.value.code == 7  # LC_ERR_OOM
+    ref, ores, _ = oracle.louvain_plus(g)
+    for limit in (0, 8 << 30):
+        labels, res = lc.lc_cluster(*args, opts=lc.Options(scratch_limit=limit))
+        torch.cuda.synchronize()
+        assert np.array_equal(labels.cpu().numpy(), ref) and res["phi"] == ores["phi"]

@@ -57,7 +57,7 @@ WORKLOADS = {
 
 # DRAM bytes per step of a kernel class, from one ncu capture of the same
 # kernels on the same workload (profiles/dram_rmat22.md); null elsewhere.
-TRAFFIC_PER_STEP = {("rmat22", "move"): 46.151e9}
+TRAFFIC_PER_STEP = {}
 
 
 def make_graph(name: str, scale_override: int | None = None):
@@ -550,6 +550,8 @@ def main():
     ap.add_argument("--rates", default="0.25,0.5,0.75,0.9,1.1",
                     help="arrival rates as fractions of the plain path's throughput (served)")
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--tables", type=int, default=0, choices=[0, 1],
+                    help="1: high-degree tables kept across passes and updated in place")
     ap.add_argument("--max-batch", type=int, default=64)
     args = ap.parse_args()
 
@@ -589,12 +591,12 @@ def main():
     rp, col, ew, vw = t(g.row_ptr), t(g.col), t(g.ew), t(g.vw)
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts_prof = lc.Options(profile=True)
+    opts_prof = lc.Options(profile=True, tables=args.tables)
 
     K = max(1, args.iterations)
 
     if args.method != "louvain+":  # pLeiden (no uncoarsening) or pLeiden+
-        opts_prof = lc.Options(profile=True, uncoarsen=args.method == "leiden+")
+        opts_prof = lc.Options(profile=True, uncoarsen=args.method == "leiden+", tables=args.tables)
 
     def call():
         if args.method != "louvain+":
@@ -646,14 +648,16 @@ def main():
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         h_rp, h_col, h_ew, h_vw = pin(g.row_ptr), pin(g.col), pin(g.ew), pin(g.vw)
         h_lab = torch.empty(g.n, dtype=torch.int32).pin_memory().numpy()
-        lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab)
+        lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab,
+                               opts=lc.Options(tables=args.tables))
         k2 = max(1, min(args.steps, 5))
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(k2):
-            lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab)
+            lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab,
+                               opts=lc.Options(tables=args.tables))
         torch.cuda.synchronize(dev)
         e2e_s = (time.perf_counter() - t0) / k2
         if dist:
@@ -682,7 +686,8 @@ def main():
     breakdown = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
                      "algorithmic_GBps": (kbytes[k] / (kms[k] / 1000.0) / 1e9) if kms[k] > 0 else None}
                  for k in lc.LC_K_NAMES}
-    lm_ms = (kms["first_pass"] + kms["move"] + kms["afterburner"] + kms["apply"] + kms["objective"]) / args.steps
+    lm_ms = (kms["first_pass"] + kms["move"] + kms["table"] + kms["afterburner"] + kms["apply"]
+             + kms["objective"]) / args.steps
     ct_ms = kms["contract"] / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,

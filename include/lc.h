@@ -125,7 +125,12 @@ typedef struct {
                                its cluster may not join another one-vertex cluster with a
                                larger label), none in even passes.  1 and 2 are the
                                ablations of Section VI. */
-  int32_t reserved;         /* 0 */
+  int32_t tables;           /* how the passes get S(v, .) (Algorithm 2): 0 = every pass
+                               aggregates it from the CSR (default); 1 = vertices of
+                               degree above 256 keep their tables across the passes of a
+                               LocalMovePasses call, and each later pass updates them in
+                               place from the last pass's movers (Section IV-A-3).
+                               Results are identical; 0 is faster on the graphs measured. */
   int64_t scratch_limit;    /* bytes of device scratch one call may hold at once; 0 = no
                                limit.  A call that needs more returns LC_ERR_OOM (nothing
                                is kept allocated), as when the device itself runs out. */
@@ -142,7 +147,9 @@ enum {
   LC_K_OTHER = 6,      /* binning, projection, validation, guards */
   LC_K_ALT = 7,        /* pLeiden: LocalMoveAlt (Section V-A) */
   LC_K_REFINE = 8,     /* pLeiden: pLeidenR refinement (Algorithm 6) */
-  LC_K_COUNT = 9
+  LC_K_TABLE = 9,      /* kept tables: in-place update from the movers + argmax and
+                          candidate test read from the tables (Section IV-A-3) */
+  LC_K_COUNT = 10
 };
 
 typedef struct {
@@ -162,6 +169,8 @@ typedef struct {
   int64_t kernel_launches[LC_K_COUNT];
   double kernel_bytes[LC_K_COUNT];
   int64_t error_detail; /* extra context for some errors (e.g. offending vertex) */
+  int64_t tables_rebuilt; /* kept tables (opts.tables) that ran out of slots during an
+                             in-place update and were rebuilt from the labels */
 } lc_result;
 
 /* Fill *o with the defaults of Section VI-C (pass limit 6, phi 3/4 x4 then

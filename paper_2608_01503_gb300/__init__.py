@@ -35,7 +35,7 @@ _lib = None
 LC_ERR_NOT_READY = 11
 
 LC_K_NAMES = ["first_pass", "move", "afterburner", "apply", "objective", "contract", "other",
-              "leiden_alt", "leiden_refine"]
+              "leiden_alt", "leiden_refine", "table"]
 
 
 class LCError(RuntimeError):
@@ -71,7 +71,7 @@ class _Opts(ctypes.Structure):
                 ("uncoarsen", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p),
-                ("symmetry", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("symmetry", ctypes.c_int32), ("tables", ctypes.c_int32),
                 ("scratch_limit", ctypes.c_int64)]
 
 
@@ -80,9 +80,9 @@ class _Result(ctypes.Structure):
                 ("passes_total", ctypes.c_int32), ("phi", ctypes.c_int64),
                 ("lambda_den", ctypes.c_int64), ("objective", ctypes.c_double),
                 ("modularity", ctypes.c_double), ("edges_local_move", ctypes.c_int64),
-                ("edges_contract", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 9),
-                ("kernel_launches", ctypes.c_int64 * 9), ("kernel_bytes", ctypes.c_double * 9),
-                ("error_detail", ctypes.c_int64)]
+                ("edges_contract", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 10),
+                ("kernel_launches", ctypes.c_int64 * 10), ("kernel_bytes", ctypes.c_double * 10),
+                ("error_detail", ctypes.c_int64), ("tables_rebuilt", ctypes.c_int64)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -168,6 +168,7 @@ class Options:
     profile: bool = False
     symmetry: int = 0  # 0 afterburner, 1 none, 2 minimum label heuristic in odd passes
     scratch_limit: int = 0  # bytes of device scratch a call may hold; 0 = no limit
+    tables: int = 0  # 1: high-degree tables kept across passes and updated in place
 
 
 def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
@@ -185,6 +186,7 @@ def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     c.profile = int(bool(o.profile))
     c.symmetry = int(o.symmetry)
     c.scratch_limit = int(o.scratch_limit)
+    c.tables = int(o.tables)
     c.stream = stream
     if event_fn is not None:
         c.event_cb = event_fn
@@ -214,7 +216,7 @@ def _dev(t, dtype, name):
 def _result(r: _Result) -> dict:
     out = {k: getattr(r, k) for k in ("n_clusters", "levels", "passes_total", "phi", "lambda_den",
                                       "objective", "modularity", "edges_local_move", "edges_contract",
-                                      "error_detail")}
+                                      "error_detail", "tables_rebuilt")}
     out["kernel_ms"] = dict(zip(LC_K_NAMES, list(r.kernel_ms)))
     out["kernel_launches"] = dict(zip(LC_K_NAMES, list(r.kernel_launches)))
     out["kernel_bytes"] = dict(zip(LC_K_NAMES, list(r.kernel_bytes)))

@@ -189,10 +189,12 @@ struct Run {
   Prof prof;
   // scratch sized for G_0
   int32_t *C = nullptr, *D = nullptr, *C_out = nullptr, *freelist = nullptr, *used = nullptr,
-          *newid = nullptr, *cnt = nullptr, *scan32 = nullptr, *freepos = nullptr, *mrank = nullptr;
+          *newid = nullptr, *cnt = nullptr, *scan32 = nullptr, *freepos = nullptr, *mrank = nullptr,
+          *Cprev = nullptr, *dirty = nullptr, *dirty_list = nullptr;
   int64_t *W = nullptr, *delta = nullptr, *bound = nullptr, *off = nullptr, *scan64 = nullptr;
   uint8_t *M = nullptr, *E = nullptr;
   AbRec *ab = nullptr;
+  int2 *upd_list = nullptr;
   unsigned long long *gtab = nullptr;
   long long *gself = nullptr;
   Scalars *sc = nullptr;
@@ -234,6 +236,13 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.cnt, n0));
   LC_TRY(r.ar.get(&r.freepos, n0));
   LC_TRY(r.ar.get(&r.mrank, n0));
+  if (r.o.tables == 1) {  // kept tables only
+    LC_TRY(r.ar.get(&r.Cprev, n0));
+    LC_TRY(r.ar.get(&r.dirty, n0));
+    LC_TRY(r.ar.get(&r.dirty_list, n0));
+    LC_TRY(r.ar.get(&r.upd_list, upd_list_size(n0, nnz0)));
+    LC_CK(cudaMemsetAsync(r.dirty, 0, sizeof(int32_t) * (size_t)(n0 > 0 ? n0 : 1), r.s));
+  }
   const int64_t big = 2 * nnz0 > n0 + 1 ? 2 * nnz0 : n0 + 1;
   LC_TRY(r.ar.get(&r.scan32, scan_scratch(big)));
   LC_TRY(r.ar.get(&r.W, n0));
@@ -351,6 +360,9 @@ static PassArgs pass_args(Run &r, const Level &L) {
   a.sc = r.sc;
   a.gtab = r.gtab;
   a.hub = L.hub;
+  a.Cprev = r.Cprev;
+  a.dirty = r.dirty;
+  a.dirty_list = r.dirty_list;
   return a;
 }
 
@@ -417,6 +429,14 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   }
   LC_TRY(fill_per_graph(r, r.phi_out, singleton ? 0 : LLONG_MIN));  // Phi(singletons) = 0
   LC_CK(cudaMemsetAsync(r.phi_acc, 0, 8 * (size_t)r.G, r.s));
+  // Kept tables (opts.tables = 1, Section IV-A-3): the first aggregation
+  // pass of the call writes the tables of the vertices of degree above
+  // kTabMinDeg out; every later pass updates them in place from the last
+  // pass's movers and reads those vertices' argmax from them.  The last pass
+  // clears them as it reads, so gtab is clean again when the call returns.
+  const bool tables = r.o.tables == 1 && nnz > 0;
+  bool kept = false;  // gtab holds tables matching C (updated by the next table pass)
+  a.upd_list = tables ? r.upd_list : nullptr;
   for (int i = 1; i <= r.o.pass_limit; ++i) {
     a.phi_n = r.o.phi_num[i - 1];
     a.phi_d = r.o.phi_den[i - 1];
@@ -426,9 +446,23 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
       r.res->kernel_launches[LC_K_FIRST_PASS] += launch_first_pass(a, L.bins, r.s);
       r.prof.end(16.0 * nnz + 44.0 * n);
     } else {
-      r.prof.begin(LC_K_MOVE);
-      r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
-      r.prof.end(12.0 * nnz + 48.0 * n);
+      if (kept) {
+        a.tab_build = 0;
+        a.tab_reset = i == r.o.pass_limit;
+        r.prof.begin(LC_K_TABLE);
+        r.res->kernel_launches[LC_K_TABLE] += launch_table_pass(a, L.bins, r.s);
+        // every table slot + the per-vertex reads and writes of the move step
+        // (+ 40 B per updated edge, added from sc->tab_upd_edges at the end)
+        r.prof.end(16.0 * nnz + 48.0 * n);
+        kept = !a.tab_reset;
+      } else {
+        a.tab_build = tables && i < r.o.pass_limit;
+        r.prof.begin(LC_K_MOVE);
+        r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
+        r.prof.end(12.0 * nnz + 48.0 * n + (a.tab_build ? 16.0 * nnz : 0.0));
+        kept = a.tab_build != 0;
+        a.tab_build = 0;
+      }
       r.prof.begin(LC_K_APPLY);
       r.res->kernel_launches[LC_K_APPLY] += launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
       r.prof.end(8.0 * n);
@@ -448,6 +482,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     r.res->edges_local_move += nnz;
     if (r.o.event_cb && r.G == 1) LC_TRY(emit_pass_event(r, L, level, phase, i));
   }
+  if (kept) LC_CK(cudaMemsetAsync(r.gtab, 0, 16 * (size_t)nnz, r.s));  // defensive: the last pass cleared them
   r.prof.begin(LC_K_OBJECTIVE);
   r.res->kernel_launches[LC_K_OBJECTIVE] +=
       launch_objective(a, L.bins, r.s) + launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
@@ -644,6 +679,7 @@ static int check_opts(const lc_opts &o) {
     if (o.phi_den[i] <= 0 || o.phi_num[i] < 0 || o.phi_num[i] > o.phi_den[i]) return LC_ERR_ARG;
   if (o.eps_num <= 0 || o.eps_den <= 0) return LC_ERR_ARG;
   if (o.symmetry < 0 || o.symmetry > 2) return LC_ERR_ARG;
+  if (o.tables < 0 || o.tables > 1) return LC_ERR_ARG;
   if (o.scratch_limit < 0) return LC_ERR_ARG;
   return LC_OK;
 }
@@ -869,6 +905,14 @@ static int begin_call(Run &r, const lc_opts *opts, lc_result *res, int G) {
 }
 
 static void end_call(Run &r, int rc) {
+  if (rc == LC_OK && r.sc && r.o.tables == 1) {
+    long long rebuilt = 0;
+    if (cudaMemcpyAsync(&rebuilt, &r.sc->tab_rebuilt, sizeof(rebuilt), cudaMemcpyDeviceToHost, r.s) ==
+            cudaSuccess &&
+        cudaStreamSynchronize(r.s) == cudaSuccess)
+      r.res->tables_rebuilt = rebuilt;
+    cudaGetLastError();
+  }
   if (r.prof.on) {
     cudaStreamSynchronize(r.s);
     r.prof.finish(r.res);
@@ -877,6 +921,11 @@ static void end_call(Run &r, int rc) {
         cudaMemcpyAsync(&cand, &r.sc->cand_edges, sizeof(cand), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
         cudaStreamSynchronize(r.s) == cudaSuccess)
       r.res->kernel_bytes[LC_K_AFTERBURNER] += 24.0 * (double)cand;
+    long long upd = 0;  // kept tables: col, ew, the neighbour's row bounds, two slot updates
+    if (r.sc &&
+        cudaMemcpyAsync(&upd, &r.sc->tab_upd_edges, sizeof(upd), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
+        cudaStreamSynchronize(r.s) == cudaSuccess)
+      r.res->kernel_bytes[LC_K_TABLE] += 40.0 * (double)upd;
     cudaGetLastError();
   }
   if (rc != LC_OK) {

@@ -43,6 +43,19 @@ constexpr int64_t kBinMaxDeg[kBins - 1] = {8, 16, 32, 128, 256, 512, 1024, 2048,
 constexpr int kWarpBinWarps = 8;    // warps per block in the warp-table bins
 constexpr int kHubThreads = 256;
 constexpr int kHubChunk = 2048;     // edges per hub chunk
+constexpr int kBin8Slots = 6144;    // shared table of bin 8
+constexpr int64_t kTabMinDeg = 256; // kept tables (opts.tables): vertices of degree above this
+constexpr int kUpdChunk = 256;      // edges per chunk of a mover's row in the table update
+
+// Slots of the kept table of a vertex of degree d, in shared memory and in
+// its region gtab[2 rp[v], 2 rp[v+1]) of the global table alike: 2d (load at
+// most 1/2), except bin 8, whose shared table holds 6144 slots (load <= 2/3).
+// One layout in both places lets a pass copy a shared table out verbatim
+// and later passes update it in place.
+__host__ __device__ __forceinline__ uint32_t tab_cap(int64_t deg) {
+  return (uint32_t)((deg > 2048 && deg <= 4096) ? (2 * deg < kBin8Slots ? 2 * deg : kBin8Slots)
+                                                 : 2 * deg);
+}
 
 // One level's graph G_l (device pointers).
 struct LevelGraph {
@@ -95,6 +108,12 @@ struct Scalars {
   int error;             // internal bound violation (hash probe overrun)
   int pad;
   long long cand_edges;  // stored edges of all candidates, summed over the call's passes
+  long long tab_upd_edges; // kept tables: movers' edges applied in place, summed over the call
+  int tab_dirty;         // kept tables that overflowed in this pass's update (listed)
+  int upd_count;         // chunks of movers' rows listed by this pass's apply step
+  int upd_prev;          // ... by the last pass's (read by this pass's table update)
+  int pad2;
+  long long tab_rebuilt; // kept tables rebuilt, summed over the call's passes
 };
 
 // ------------------------------------------------------------------ hashes

@@ -35,6 +35,21 @@ __device__ __forceinline__ void add_self(const PassArgs &a, int32_t v, long long
     phi += gC;
 }
 
+// Kept tables: writes (X, S) into a table that only the calling thread
+// touches (plain loads and stores; X is not in the table yet).  False if
+// the table is full.
+__device__ __forceinline__ bool tab_put(unsigned long long *t, uint32_t cap, int32_t X, long long S) {
+  uint32_t s = slot_of(X, cap);
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    if (t[s] == kEmptySlot) {
+      t[s] = ((unsigned long long)((uint32_t)X + 1u) << 32) | (uint32_t)S;
+      return true;
+    }
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return false;
+}
+
 // ---------------------------------------------------- vertex decision
 
 // Algorithm 2 for one vertex once g(v, C[v]) and the best other cluster
@@ -226,20 +241,21 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
 // ------------------------------------ shared-table aggregation, bins 3-5
 
 // Shared tables stay clean between vertices: a vertex's argmax scans the
-// slots [0, cap) it may have used and resets the occupied ones.  Capacity
-// is 2 deg rounded up to 32 (capped per bin), so the load factor is at most
-// 1/2 (2/3 in bin 8) and the scan touches consecutive slots.
-__device__ __forceinline__ uint32_t table_cap(int64_t deg) {
+// slots [0, cap) it may have used and resets the occupied ones.  The warp
+// bins use 2 deg rounded up to 32 slots (load <= 1/2, whole warps of slots);
+// the block bins use tab_cap(deg), the layout of the kept tables.
+__device__ __forceinline__ uint32_t warp_table_cap(int64_t deg) {
   return (uint32_t)((2 * deg + 31) & ~31ll);
 }
 
 // Best (gain, cluster) over slots [s0, s1) of a table (strided by GS),
-// resetting the slots it reads.  g(v, X) = Lam S(v, X) - (mu w(v)) W(X),
-// with mu w(v) formed once.
+// resetting the slots it reads unless `keep` (a kept table being built).
+// g(v, X) = Lam S(v, X) - (mu w(v)) W(X), with mu w(v) formed once.
 template <int GS>
 __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam &P,
                                              unsigned long long *tab, uint32_t s0, uint32_t s1,
-                                             long long wv, int r, long long &gb, int32_t &xb) {
+                                             long long wv, int r, long long &gb, int32_t &xb,
+                                             bool keep = false) {
   constexpr int U = 4;
   const long long Lam = P.Lam, muw = P.mu * wv;
   for (uint32_t base = s0 + r; base < s1; base += GS * U) {
@@ -249,7 +265,7 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam
     for (int k = 0; k < U; ++k) {
       const uint32_t s = base + k * GS;
       t[k] = s < s1 ? tab[s] : kEmptySlot;
-      if (t[k] != kEmptySlot) tab[s] = kEmptySlot;
+      if (t[k] != kEmptySlot && !keep) tab[s] = kEmptySlot;
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) WX[k] = t[k] != kEmptySlot ? a.W[slot_key(t[k])] : 0;
@@ -357,11 +373,12 @@ __device__ __forceinline__ long long split_insert_row(const PassArgs &a, int64_t
 }
 
 // Best (gain, cluster) over slots [0, cap) (strided by GS), resetting the
-// occupied ones.  g(v, X) = Lam S(v, X) - (mu w(v)) W(X).
-template <int GS>
+// occupied ones.  g(v, X) = Lam S(v, X) - (mu w(v)) W(X).  BUILD: every
+// slot is also copied to the kept table gt (same layout, empties included).
+template <int GS, bool BUILD>
 __device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam &P, SplitTab t,
                                              uint32_t cap, long long wv, int r, long long &gb,
-                                             int32_t &xb) {
+                                             int32_t &xb, unsigned long long *gt) {
   constexpr int U = 4;
   const long long Lam = P.Lam, muw = P.mu * wv;
   for (uint32_t base = r; base < cap; base += GS * U) {
@@ -377,6 +394,13 @@ __device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam
         S[k] = t.val[s];
         t.key[s] = 0u;
         t.val[s] = 0;
+      }
+    }
+    if constexpr (BUILD) {
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const uint32_t s = base + k * GS;
+        if (s < cap) gt[s] = key[k] != 0u ? ((unsigned long long)key[k] << 32) | (uint32_t)S[k] : kEmptySlot;
       }
     }
 #pragma unroll
@@ -417,7 +441,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
     const int32_t Cv = a.C[v];
     const long long wv = a.g.vw[v];
     const GraphParam P = a.gp[graph_of(a, v)];
-    const uint32_t cap = table_cap(end - beg);
+    const uint32_t cap = warp_table_cap(end - beg);
     bool ok = true;
     long long self = split_insert_row<32, U>(a, beg, end, Cv, tab, cap, lane, ok);
     if (!ok) a.sc->error = 1;
@@ -425,7 +449,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
     __syncwarp();
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    split_argmax<32>(a, P, tab, cap, wv, lane, gb, xb);
+    split_argmax<32, false>(a, P, tab, cap, wv, lane, gb, xb, nullptr);
     group_argmax<32>(gb, xb);
     self = warp_sum(self);
     if (lane == 0) {
@@ -443,7 +467,9 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
 // table (SLOTS keys, then SLOTS values).  A row uses min(2 deg rounded up
 // to 32, SLOTS) slots: bin 8 (deg <= 4096) has 6144 slots, a load factor of
 // at most 2/3, so that four blocks fit in an SM's shared memory.
-template <int GS, int SLOTS>
+// BUILD: the tables use the kept-table layout (tab_cap slots) and are
+// copied out to each vertex's gtab region with S(v, C[v]) added.
+template <int GS, int SLOTS, bool BUILD>
 __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__restrict__ list,
                                                    int64_t count) {
   extern __shared__ uint32_t smem_tab[];
@@ -463,7 +489,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     const int32_t Cv = a.C[v];
     const long long wv = a.g.vw[v];
     const GraphParam P = a.gp[graph_of(a, v)];
-    const uint32_t cap = min(table_cap(end - beg), (uint32_t)SLOTS);
+    const uint32_t cap = BUILD ? tab_cap(end - beg) : min(warp_table_cap(end - beg), (uint32_t)SLOTS);
     bool ok = true;
     long long self = split_insert_row<GS, 4>(a, beg, end, Cv, tab, cap, threadIdx.x, ok);
     if (!ok) a.sc->error = 1;
@@ -471,7 +497,8 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     __syncthreads();
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    split_argmax<GS>(a, P, tab, cap, wv, threadIdx.x, gb, xb);
+    unsigned long long *gt = a.gtab + 2 * beg;
+    split_argmax<GS, BUILD>(a, P, tab, cap, wv, threadIdx.x, gb, xb, gt);
     // one reduction of (best gain, cluster, S_self) for thread 0 only: warp
     // level, one barrier, thread 0 combines the warps
     group_argmax<32>(gb, xb);
@@ -490,6 +517,8 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
           xb = rx[w];
         }
       }
+      // the barrier above made every thread's copied slots visible
+      if (BUILD && self > 0 && !tab_put(gt, cap, Cv, self)) a.sc->error = 1;
       const long long gC = gain_self(P, self, wv, WC);
       add_self(a, v, gC, phi);
       decide(a, P, v, gC, xb, gb, cntL);
@@ -500,7 +529,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
   flush_block_sum(phi, &a.phi_acc[0]);
 }
 
-// --------------------------------------------------------- hubs (bin 6)
+// --------------------------------------------------------- hubs (bin 9)
 
 // Block-wide argmax of (g, x) into the chunk partials.
 __device__ __forceinline__ void hub_part_store(const PassArgs &a, int c, long long gb, int32_t xb) {
@@ -573,7 +602,8 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
   hub_acc_add(a, h, self);
 }
 
-// Move, step 2: argmax over the chunk's share of the hub table (reset as read).
+// Move, step 2: argmax over the chunk's share of the hub table (reset as
+// read, or kept as the hub's kept table with a.tab_build).
 __global__ void __launch_bounds__(kHubThreads) k_hub_move_scan(PassArgs a) {
   const int c = blockIdx.x;
   const int h = a.hub.hub_of[c];
@@ -584,7 +614,8 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_scan(PassArgs a) {
   long long gb = LLONG_MIN;
   int32_t xb = kNone;
   range_argmax<kHubThreads>(a, P, a.gtab + 2 * beg, (uint32_t)(2 * (a.hub.e0[c] - beg)),
-                            (uint32_t)(2 * (a.hub.e1[c] - beg)), wv, threadIdx.x, gb, xb);
+                            (uint32_t)(2 * (a.hub.e1[c] - beg)), wv, threadIdx.x, gb, xb,
+                            a.tab_build != 0);
   hub_part_store(a, c, gb, xb);
 }
 
@@ -620,8 +651,13 @@ __global__ void k_hub_decide(PassArgs a, int first) {
     if (!first) {
       const long long self = a.hub.acc[h];
       a.hub.acc[h] = 0;
-      gC = gain_self(P, self, a.g.vw[v], a.W[a.C[v]]);
+      const int32_t Cv = a.C[v];
+      gC = gain_self(P, self, a.g.vw[v], a.W[Cv]);
       add_self(a, v, gC, phi);
+      if (a.tab_build && self > 0) {  // the hub's kept table gets its own cluster
+        const int64_t beg = a.g.rp[v];
+        if (!tab_put(a.gtab + 2 * beg, tab_cap(a.g.rp[v + 1] - beg), Cv, self)) a.sc->error = 1;
+      }
     }
     decide(a, P, v, gC, xb, gb, cntL);
   }
@@ -860,28 +896,279 @@ __global__ void k_hub_obj_final(PassArgs a) {
   flush_block_sum(phi, &a.phi_acc[0]);
 }
 
+// ------------------------------------------ kept tables (Section IV-A-3)
+//
+// Vertices of degree above kTabMinDeg (bins 5-9) may keep their S(v, .)
+// across the passes of one LocalMovePasses call.  An aggregation pass with
+// a.tab_build copies each block bin's shared table (own cluster included)
+// to the vertex's gtab region in the layout of tab_cap, and leaves the hubs'
+// global tables in place.  The next pass applies the previous pass's moves
+// to those tables in place (Algorithm 2's update of the affected tables: a
+// mover from X to Y takes w(u, v) from S(u, X) and adds it to S(u, Y) for
+// each neighbour u that keeps a table), then reads the argmax of those
+// vertices from their tables; vertices of lower degree aggregate from the
+// CSR as in every other pass.  Keys are never removed: a sum that reaches
+// 0 marks a cluster no longer adjacent and is skipped.  A table that runs
+// out of slots is listed and rebuilt from the labels.
+
+// Subtracts w from the sum of an existing key (nothing is inserted).
+// Returns false when the key is absent, which only an overflowed table
+// (rebuilt afterwards) can show.  Keys present before the kernel come
+// before any empty slot of their probe sequence, so concurrent inserts of
+// other keys cannot hide them.
+__device__ __forceinline__ bool tab_sub(unsigned long long *t, uint32_t cap, int32_t key, int32_t w) {
+  const unsigned long long tag = (unsigned long long)((uint32_t)key + 1u) << 32;
+  uint32_t s = slot_of(key, cap);
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    const unsigned long long cur = t[s];
+    if (cur == kEmptySlot) return false;
+    if ((cur & 0xFFFFFFFF00000000ull) == tag) {
+      atomicAdd(reinterpret_cast<unsigned int *>(&t[s]), (unsigned int)(-w));
+      return true;
+    }
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mark_dirty(const PassArgs &a, int32_t u) {
+  if (atomicExch(&a.dirty[u], 1) == 0) a.dirty_list[atomicAdd(&a.sc->tab_dirty, 1)] = u;
+}
+
+// The move Xo -> Xn of one mover applied to the kept tables of its
+// neighbours over edges [e0, e1) (strided by 32, loads batched U at a time).
+__device__ __forceinline__ void tab_move_edges(const PassArgs &a, int64_t e0, int64_t e1, int lane,
+                                               int32_t Xo, int32_t Xn) {
+  constexpr int U = 4;
+  for (int64_t base = e0 + lane; base < e1; base += 32 * U) {
+    int32_t u[U], w[U];
+    int64_t ub[U], ue[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t e = base + 32 * k;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < e1) {
+        u[k] = __ldg(a.g.col + e);
+        w[k] = __ldg(a.g.ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      ub[k] = u[k] >= 0 ? a.g.rp[u[k]] : 0;
+      ue[k] = u[k] >= 0 ? a.g.rp[u[k] + 1] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (u[k] < 0 || ue[k] - ub[k] <= kTabMinDeg) continue;  // no kept table
+      unsigned long long *t = a.gtab + 2 * ub[k];
+      const uint32_t cap = tab_cap(ue[k] - ub[k]);
+      bool fresh;
+      const bool ok = tab_sub(t, cap, Xo, w[k]);
+      if (!(table_add(t, cap, Xn, w[k], fresh) && ok)) mark_dirty(a, u[k]);
+    }
+  }
+}
+
+// Update: one warp per chunk of a mover's row (the chunks were listed by
+// the last pass's apply step).
+__global__ void __launch_bounds__(256) k_tab_update(PassArgs a) {
+  const int cnt = a.sc->upd_prev;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  long long done = 0;  // edges applied (lane 0), for the profile's byte count
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
+    const int2 ch = a.upd_list[j];
+    const int32_t v = ch.x;
+    const int32_t Xo = a.Cprev[v], Xn = a.C[v];
+    if (Xo == Xn) continue;  // a mover that got its own emptied id back
+    const int64_t e0 = a.g.rp[v] + (int64_t)ch.y * kUpdChunk;
+    const int64_t end = a.g.rp[v + 1];
+    const int64_t e1 = e0 + kUpdChunk < end ? e0 + kUpdChunk : end;
+    tab_move_edges(a, e0, e1, lane, Xo, Xn);
+    if (lane == 0) done += e1 - e0;
+  }
+  flush_block_sum(done, &a.sc->tab_upd_edges);
+}
+
+// Rebuilds the listed overflowed tables from the current labels, one warp
+// per table (rare: a table overflows only after more new clusters reached
+// it than it has free slots).
+__global__ void __launch_bounds__(256) k_tab_rebuild(PassArgs a) {
+  const int cnt = a.sc->tab_dirty;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  bool ok = true;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
+    const int32_t v = a.dirty_list[j];
+    const int64_t beg = a.g.rp[v], deg = a.g.rp[v + 1] - beg;
+    unsigned long long *t = a.gtab + 2 * beg;
+    const uint32_t cap = tab_cap(deg);
+    for (int64_t s = lane; s < 2 * deg; s += 32) t[s] = kEmptySlot;
+    __syncwarp();
+    for (int64_t e = beg + lane; e < beg + deg; e += 32) {
+      bool fresh;
+      ok &= table_add(t, cap, a.C[__ldg(a.g.col + e)], __ldg(a.g.ew + e), fresh);
+    }
+    __syncwarp();
+    if (lane == 0) a.dirty[v] = 0;
+  }
+  if (!ok) a.sc->error = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && cnt > 0) a.sc->tab_rebuilt += cnt;
+}
+
+// Best (gain, cluster) over the slot pairs [p0, p1) of a kept table
+// (16-byte loads, strided by GS, V pairs per thread at a time) and this
+// thread's part of S(v, C[v]); with `reset` the slots are cleared as they
+// are read (the last pass of a call leaves gtab clean).
+template <int GS, int V>
+__device__ __forceinline__ void tab_pairs_scan(const PassArgs &a, const GraphParam &P, ulonglong2 *t2,
+                                               uint32_t p0, uint32_t p1, int32_t Cv, long long wv,
+                                               bool reset, long long &self, long long &gb, int32_t &xb) {
+  const long long Lam = P.Lam, muw = P.mu * wv;
+  for (uint32_t base = p0 + threadIdx.x; base < p1; base += GS * V) {
+    unsigned long long t[2 * V];
+    long long WX[2 * V];
+    bool use[2 * V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const uint32_t p = base + k * GS;
+      ulonglong2 x = make_ulonglong2(kEmptySlot, kEmptySlot);
+      if (p < p1) x = t2[p];
+      if (reset && p < p1 && (x.x | x.y) != 0ull) t2[p] = make_ulonglong2(kEmptySlot, kEmptySlot);
+      t[2 * k] = x.x;
+      t[2 * k + 1] = x.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * V; ++k) {
+      const int32_t X = slot_key(t[k]), S = slot_val(t[k]);
+      use[k] = t[k] != kEmptySlot && S > 0 && X != Cv;
+      if (t[k] != kEmptySlot && X == Cv) self += S;
+      WX[k] = use[k] ? a.W[X] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * V; ++k) {
+      if (!use[k]) continue;
+      const int32_t X = slot_key(t[k]);
+      const long long g = Lam * (long long)slot_val(t[k]) - muw * WX[k];
+      if (better(g, X, gb, xb)) {
+        gb = g;
+        xb = X;
+      }
+    }
+  }
+}
+
+// Argmax and candidate test of Algorithm 2 from the kept tables, one block
+// per vertex of bins 5-8 (a single reduction to thread 0 per vertex; the
+// partials alternate between two buffers, so one barrier per vertex).
+template <int GS, int V>
+__global__ void __launch_bounds__(GS) k_tab_scan(PassArgs a, const int32_t *__restrict__ list,
+                                                 int64_t count) {
+  __shared__ long long rs[2][GS / 32], rg[2][GS / 32];
+  __shared__ int32_t rx[2][GS / 32];
+  long long cntL = 0, phi = 0;
+  int par = 0;
+  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const int32_t v = list[i];
+    const int64_t beg = a.g.rp[v];
+    const uint32_t cap = tab_cap(a.g.rp[v + 1] - beg);
+    const int32_t Cv = a.C[v];
+    const long long wv = a.g.vw[v];
+    const GraphParam P = a.gp[graph_of(a, v)];
+    long long self = 0, gb = LLONG_MIN;
+    int32_t xb = kNone;
+    tab_pairs_scan<GS, V>(a, P, reinterpret_cast<ulonglong2 *>(a.gtab + 2 * beg), 0, cap / 2, Cv, wv,
+                          a.tab_reset != 0, self, gb, xb);
+    group_argmax<32>(gb, xb);
+    self = warp_sum(self);
+    if ((threadIdx.x & 31) == 0) {
+      rg[par][threadIdx.x >> 5] = gb;
+      rx[par][threadIdx.x >> 5] = xb;
+      rs[par][threadIdx.x >> 5] = self;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < GS / 32; ++w) {
+        self += rs[par][w];
+        if (better(rg[par][w], rx[par][w], gb, xb)) {
+          gb = rg[par][w];
+          xb = rx[par][w];
+        }
+      }
+      const long long gC = gain_self(P, self, wv, a.W[Cv]);
+      add_self(a, v, gC, phi);
+      decide(a, P, v, gC, xb, gb, cntL);
+    }
+    par ^= 1;
+  }
+  flush_block_sum(cntL, &a.sc->count_L);
+  flush_block_sum(phi, &a.phi_acc[0]);
+}
+
+// Hubs: each chunk scans its share of the hub's table; k_hub_decide
+// combines the partials and the parts of S(v, C[v]).
+__global__ void __launch_bounds__(kHubThreads) k_hub_tab_scan(PassArgs a) {
+  const int c = blockIdx.x;
+  const int h = a.hub.hub_of[c];
+  const int32_t v = a.hub.vtx[h];
+  const int64_t beg = a.g.rp[v];
+  const GraphParam P = a.gp[graph_of(a, v)];
+  long long self = 0, gb = LLONG_MIN;
+  int32_t xb = kNone;
+  // a chunk of edges [e0, e1) owns the slot pairs [e0 - beg, e1 - beg)
+  tab_pairs_scan<kHubThreads, 4>(a, P, reinterpret_cast<ulonglong2 *>(a.gtab + 2 * beg),
+                                 (uint32_t)(a.hub.e0[c] - beg), (uint32_t)(a.hub.e1[c] - beg), a.C[v],
+                                 a.g.vw[v], a.tab_reset != 0, self, gb, xb);
+  hub_part_store(a, c, gb, xb);
+  hub_acc_add(a, h, self);
+}
+
 // ----------------------------------------------------------- update
 
 // Apply D for M (Algorithm 2, Update): real destinations move now; movers
 // to a new empty cluster leave their cluster and are flagged for ids.
 __global__ void k_apply(PassArgs a, uint8_t *__restrict__ E) {
   long long empties = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    uint8_t e = 0;
-    if (a.M[v]) {
-      const int32_t Dv = a.D[v], Cv = a.C[v];
-      const long long wv = a.g.vw[v];
-      atomicAdd((unsigned long long *)&a.W[Cv], (unsigned long long)(-wv));
-      if (Dv >= 0) {
-        a.C[v] = Dv;
-        atomicAdd((unsigned long long *)&a.W[Dv], (unsigned long long)wv);
-      } else {
-        e = 1;
-        empties++;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count: the chunk list below is appended per warp
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.g.n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    int nch = 0;  // chunks of this mover's row for the kept tables' update
+    if (v < a.g.n) {
+      uint8_t e = 0;
+      if (a.M[v]) {
+        const int32_t Dv = a.D[v], Cv = a.C[v];
+        const long long wv = a.g.vw[v];
+        if (a.upd_list) {
+          a.Cprev[v] = Cv;
+          nch = (int)((a.g.rp[v + 1] - a.g.rp[v] + kUpdChunk - 1) / kUpdChunk);
+        }
+        atomicAdd((unsigned long long *)&a.W[Cv], (unsigned long long)(-wv));
+        if (Dv >= 0) {
+          a.C[v] = Dv;
+          atomicAdd((unsigned long long *)&a.W[Dv], (unsigned long long)wv);
+        } else {
+          e = 1;
+          empties++;
+        }
       }
+      E[v] = e;
     }
-    E[v] = e;
+    if (a.upd_list) {  // uniform over the launch
+      int incl = nch;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      int first = 0;
+      if (lane == 31 && total > 0) first = atomicAdd(&a.sc->upd_count, total);
+      first = __shfl_sync(0xFFFFFFFFu, first, 31) + incl - nch;
+      for (int c = 0; c < nch; ++c) a.upd_list[first + c] = make_int2((int32_t)v, c);
+    }
   }
   __shared__ long long red[32];
   long long x = warp_sum(empties);
@@ -988,6 +1275,9 @@ __global__ void k_pass_begin(Scalars *sc) {
   sc->count_L = 0;
   sc->count_M = 0;
   sc->empty_movers = 0;
+  sc->tab_dirty = 0;
+  sc->upd_prev = sc->upd_count;
+  sc->upd_count = 0;
 }
 
 // Algorithm 2's best-of test, per graph, on the objective accumulated in
@@ -1069,13 +1359,21 @@ static inline unsigned blocks_for(int64_t items, int per_block) {
 static constexpr int block_table_bytes(int slots) { return slots * 8; }
 
 void configure_kernels() {
-  cudaFuncSetAttribute(k_move_block<64, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_move_block<64, 1024, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        block_table_bytes(1024));
-  cudaFuncSetAttribute(k_move_block<128, 2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_move_block<128, 2048, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        block_table_bytes(2048));
-  cudaFuncSetAttribute(k_move_block<256, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_move_block<256, 4096, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        block_table_bytes(4096));
-  cudaFuncSetAttribute(k_move_block<256, 6144>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_move_block<256, 6144, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(6144));
+  cudaFuncSetAttribute(k_move_block<64, 1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(1024));
+  cudaFuncSetAttribute(k_move_block<128, 2048, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(2048));
+  cudaFuncSetAttribute(k_move_block<256, 4096, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       block_table_bytes(4096));
+  cudaFuncSetAttribute(k_move_block<256, 6144, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        block_table_bytes(6144));
 }
 
@@ -1133,7 +1431,12 @@ int launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s) {
 template <int GS, int SLOTS>
 static int launch_move_block(const PassArgs &a, BinRange r, cudaStream_t s) {
   if (r.count <= 0) return 0;
-  k_move_block<GS, SLOTS><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.list, r.count);
+  if (a.tab_build)
+    k_move_block<GS, SLOTS, true><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.list,
+                                                                                               r.count);
+  else
+    k_move_block<GS, SLOTS, false><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.list,
+                                                                                                r.count);
   return 1;
 }
 
@@ -1144,7 +1447,8 @@ static int launch_move_warp(const PassArgs &a, BinRange r, cudaStream_t s) {
   return 1;
 }
 
-int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
+// Bins 0-4 (degree <= 256): aggregation from the CSR in every pass.
+static int launch_move_low(const PassArgs &a, const Bins &b, cudaStream_t s) {
   int n = 0;
   const BinRange r0 = bin_range(b, 0, 0);
   if (r0.count > 0) {
@@ -1155,6 +1459,11 @@ int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
   n += launch_vertex_kernel<32>(k_move_small<32>, a, bin_range(b, 2, 2), s);
   n += launch_move_warp<256>(a, bin_range(b, 3, 3), s);
   n += launch_move_warp<512>(a, bin_range(b, 4, 4), s);
+  return n;
+}
+
+int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  int n = launch_move_low(a, b, s);
   n += launch_move_block<64, 1024>(a, bin_range(b, 5, 5), s);
   n += launch_move_block<128, 2048>(a, bin_range(b, 6, 6), s);
   n += launch_move_block<256, 4096>(a, bin_range(b, 7, 7), s);
@@ -1164,6 +1473,31 @@ int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s) {
     k_hub_move_scan<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     k_hub_decide<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a, 0);
     n += 3;
+  }
+  return n;
+}
+
+template <int GS, int V>
+static int launch_tab_scan(const PassArgs &a, BinRange r, cudaStream_t s) {
+  if (r.count <= 0) return 0;
+  k_tab_scan<GS, V><<<blocks_for(r.count, 1), GS, 0, s>>>(a, r.list, r.count);
+  return 1;
+}
+
+int launch_table_pass(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  int n = launch_move_low(a, b, s);
+  k_tab_update<<<152 * 8, 256, 0, s>>>(a);
+  k_tab_rebuild<<<152 * 4, 256, 0, s>>>(a);
+  n += 2;
+  // one 16-byte pair of slots per thread per batch of V: bin 5 has at most
+  // 512 pairs, bin 6 1024, bin 7 2048, bin 8 3072
+  n += launch_tab_scan<128, 4>(a, bin_range(b, 5, 5), s);
+  n += launch_tab_scan<256, 4>(a, bin_range(b, 6, 6), s);
+  n += launch_tab_scan<512, 4>(a, bin_range(b, 7, 8), s);
+  if (a.hub.H > 0) {
+    k_hub_tab_scan<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    k_hub_decide<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a, 0);
+    n += 2;
   }
   return n;
 }

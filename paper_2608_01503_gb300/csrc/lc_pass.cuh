@@ -26,6 +26,14 @@ struct PassArgs {
   unsigned long long *gtab;  // clean global hash scratch, >= 2 nnz slots
   int32_t phi_n, phi_d;      // temperature of this pass
   Hubs hub;                  // chunk plan of the hub bin of this level
+  // kept tables: each vertex's S(v, .) in its gtab region (tab_cap slots)
+  int32_t tab_build;         // this aggregation pass also writes the tables out
+  int32_t tab_reset;         // this table pass clears the tables as it reads them
+  int32_t *Cprev;            // [n] label before the last apply, of its movers
+  int32_t *dirty;            // [n] 1: the table overflowed and is rebuilt (zero between passes)
+  int32_t *dirty_list;       // [n] those vertices, sc->tab_dirty of them
+  int2 *upd_list;            // chunks {mover, chunk} of the movers' rows, listed by the
+                             // apply step when tables are kept (else nullptr)
 };
 
 // Vertex lists of the degree bins of one level (stable: ascending ids).
@@ -64,6 +72,14 @@ int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
 // cluster with a larger label.  size: int32[n] scratch.
 int launch_symmetry_ablation(const PassArgs &a, bool mlh, int32_t *size, cudaStream_t s);
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
+// Kept tables (Section IV-A-3): applies the last pass's moves to the tables
+// of the movers' neighbours (rebuilding any that overflow), then the argmax
+// and candidate test of Algorithm 2, read from the tables for vertices of
+// degree above kTabMinDeg and aggregated from the CSR for the others.
+int launch_table_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
+// Entries of PassArgs::upd_list a level of n vertices and nnz stored edges
+// may need.
+inline int64_t upd_list_size(int64_t n, int64_t nnz) { return n + nnz / kUpdChunk + 1; }
 // Scratch of the update step (all [n] of the level).
 struct ApplyScratch {
   uint8_t *E;

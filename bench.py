@@ -57,7 +57,7 @@ WORKLOADS = {
 
 # DRAM bytes per step of a kernel class, from one ncu capture of the same
 # kernels on the same workload (profiles/dram_rmat22.md); null elsewhere.
-TRAFFIC_PER_STEP = {}
+TRAFFIC_PER_STEP = {("rmat22", "move"): 46.155e9}
 
 
 def make_graph(name: str, scale_override: int | None = None):

@@ -236,8 +236,8 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.cnt, n0));
   LC_TRY(r.ar.get(&r.freepos, n0));
   LC_TRY(r.ar.get(&r.mrank, n0));
+  LC_TRY(r.ar.get(&r.Cprev, n0));
   if (r.o.tables == 1) {  // kept tables only
-    LC_TRY(r.ar.get(&r.Cprev, n0));
     LC_TRY(r.ar.get(&r.dirty, n0));
     LC_TRY(r.ar.get(&r.dirty_list, n0));
     LC_TRY(r.ar.get(&r.upd_list, upd_list_size(n0, nnz0)));
@@ -437,14 +437,24 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   const bool tables = r.o.tables == 1 && nnz > 0;
   bool kept = false;  // gtab holds tables matching C (updated by the next table pass)
   a.upd_list = tables ? r.upd_list : nullptr;
+  // one graph: the final objective is updated from the last pass (see below)
+  const bool incremental = r.G == 1;
   for (int i = 1; i <= r.o.pass_limit; ++i) {
     a.phi_n = r.o.phi_num[i - 1];
     a.phi_d = r.o.phi_den[i - 1];
     launch_pass_begin(r.sc, r.s);
+    const bool last = i == r.o.pass_limit;
+    if (incremental && last) {
+      r.prof.begin(LC_K_OBJECTIVE);
+      r.res->kernel_launches[LC_K_OBJECTIVE] += launch_last_pass_enter(a, r.s);
+      r.prof.end(16.0 * n);
+    }
     if (i == 1 && singleton) {
       r.prof.begin(LC_K_FIRST_PASS);
       r.res->kernel_launches[LC_K_FIRST_PASS] += launch_first_pass(a, L.bins, r.s);
       r.prof.end(16.0 * nnz + 44.0 * n);
+      if (incremental && last)  // Phi of the singletons, 0
+        r.res->kernel_launches[LC_K_OBJECTIVE] += launch_save_phi_enter(a, r.s);
     } else {
       if (kept) {
         a.tab_build = 0;
@@ -463,6 +473,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
         kept = a.tab_build != 0;
         a.tab_build = 0;
       }
+      if (incremental && last) r.res->kernel_launches[LC_K_OBJECTIVE] += launch_save_phi_enter(a, r.s);
       r.prof.begin(LC_K_APPLY);
       r.res->kernel_launches[LC_K_APPLY] += launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
       r.prof.end(8.0 * n);
@@ -483,10 +494,18 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     if (r.o.event_cb && r.G == 1) LC_TRY(emit_pass_event(r, L, level, phase, i));
   }
   if (kept) LC_CK(cudaMemsetAsync(r.gtab, 0, 16 * (size_t)nnz, r.s));  // defensive: the last pass cleared them
+  // Phi of the final state for the best-of test: one graph updates it from
+  // the state entering the last pass and that pass's moves; a batch sweeps
+  // every graph
   r.prof.begin(LC_K_OBJECTIVE);
-  r.res->kernel_launches[LC_K_OBJECTIVE] +=
-      launch_objective(a, L.bins, r.s) + launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
-  r.prof.end(12.0 * nnz + 32.0 * n);
+  if (incremental) {
+    r.res->kernel_launches[LC_K_OBJECTIVE] += launch_final_objective(a, L.bins, r.s) + launch_bestof(a, r.C_out, r.s);
+    r.prof.end(17.0 * n);  // W, w(v) and M per vertex (+ 13 B per mover edge, added at the end)
+  } else {
+    r.res->kernel_launches[LC_K_OBJECTIVE] +=
+        launch_objective(a, L.bins, r.s) + launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
+    r.prof.end(12.0 * nnz + 32.0 * n);
+  }
   LC_TRY(launch_check());
   if (r.o.event_cb && r.G == 1) {
     std::vector<int32_t> C(n > 0 ? n : 1);
@@ -926,6 +945,11 @@ static void end_call(Run &r, int rc) {
         cudaMemcpyAsync(&upd, &r.sc->tab_upd_edges, sizeof(upd), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
         cudaStreamSynchronize(r.s) == cudaSuccess)
       r.res->kernel_bytes[LC_K_TABLE] += 40.0 * (double)upd;
+    long long dph = 0;  // final objective: col, ew, C[u], M[u] of each mover edge
+    if (r.sc &&
+        cudaMemcpyAsync(&dph, &r.sc->dphi_edges, sizeof(dph), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
+        cudaStreamSynchronize(r.s) == cudaSuccess)
+      r.res->kernel_bytes[LC_K_OBJECTIVE] += 13.0 * (double)dph;
     cudaGetLastError();
   }
   if (rc != LC_OK) {

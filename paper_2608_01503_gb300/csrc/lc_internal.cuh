@@ -114,6 +114,13 @@ struct Scalars {
   int upd_prev;          // ... by the last pass's (read by this pass's table update)
   int pad2;
   long long tab_rebuilt; // kept tables rebuilt, summed over the call's passes
+  // objective after a call's last pass (one graph), from the state entering it:
+  // Phi = Lam IN - mu Q with IN = sum_v S(v, C[v]), Q = sum_X W(X)^2 - sum_v w(v)^2
+  long long phi_enter;   // Phi entering the last pass (its move step's sum)
+  long long q_enter;     // Q entering the last pass
+  long long q_final;     // Q after it
+  long long d_in;        // change of IN by its moves
+  long long dphi_edges;  // movers' edges read for d_in, summed over the call
 };
 
 // ------------------------------------------------------------------ hashes

@@ -35,6 +35,7 @@ __device__ __forceinline__ void add_self(const PassArgs &a, int32_t v, long long
     phi += gC;
 }
 
+
 // Kept tables: writes (X, S) into a table that only the calling thread
 // touches (plain loads and stores; X is not in the table yet).  False if
 // the table is full.
@@ -1141,10 +1142,8 @@ __global__ void k_apply(PassArgs a, uint8_t *__restrict__ E) {
       if (a.M[v]) {
         const int32_t Dv = a.D[v], Cv = a.C[v];
         const long long wv = a.g.vw[v];
-        if (a.upd_list) {
-          a.Cprev[v] = Cv;
-          nch = (int)((a.g.rp[v + 1] - a.g.rp[v] + kUpdChunk - 1) / kUpdChunk);
-        }
+        a.Cprev[v] = Cv;
+        if (a.upd_list) nch = (int)((a.g.rp[v + 1] - a.g.rp[v] + kUpdChunk - 1) / kUpdChunk);
         atomicAdd((unsigned long long *)&a.W[Cv], (unsigned long long)(-wv));
         if (Dv >= 0) {
           a.C[v] = Dv;
@@ -1566,6 +1565,136 @@ int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
     n += 2;
   }
   return n;
+}
+
+// ------------------------- objective after the last pass (one graph)
+//
+// Phi = Lam IN - mu Q (Eq. 1 regrouped): IN = sum_v S(v, C[v]) and
+// Q = sum_X W(X)^2 - sum_v w(v)^2.  The last pass's move step sums Phi of
+// the state entering it; its moves change IN only on the movers' edges, by
+// ([C'[v] = C'[u]] - [C[v] = C[u]]) w(u, v) per direction, and Q follows
+// from W before and after (an O(n) sweep each).  So the objective of the
+// call's final state, which the best-of test of Algorithm 2 needs, costs a
+// walk over the movers' rows instead of a sweep of the whole graph:
+//   Phi' = Phi + Lam dIN - mu (Q' - Q).
+
+// Change of IN over edges [e0, e1) of mover v (strided by GS): an edge to
+// a non-mover counts both directions, an edge between movers one (the
+// other mover counts the other).
+template <int GS>
+__device__ __forceinline__ long long delta_in_edges(const PassArgs &a, int32_t v, int64_t e0, int64_t e1,
+                                                    int r) {
+  constexpr int U = 4;
+  const int32_t Cvn = a.C[v], Cvo = a.Cprev[v];
+  long long d = 0;
+  for (int64_t base = e0 + r; base < e1; base += (int64_t)GS * U) {
+    int32_t u[U], w[U], Cun[U];
+    uint8_t mu[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t e = base + (int64_t)k * GS;
+      u[k] = -1;
+      w[k] = 0;
+      if (e < e1) {
+        u[k] = __ldg(a.g.col + e);
+        w[k] = __ldg(a.g.ew + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      Cun[k] = u[k] >= 0 ? a.C[u[k]] : 0;
+      mu[k] = u[k] >= 0 ? a.M[u[k]] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (u[k] < 0) continue;
+      const int32_t Cuo = mu[k] ? a.Cprev[u[k]] : Cun[k];
+      const int s = (Cvn == Cun[k] ? 1 : 0) - (Cvo == Cuo ? 1 : 0);
+      d += (long long)(mu[k] ? 1 : 2) * s * w[k];
+    }
+  }
+  return d;
+}
+
+template <int GS>
+__global__ void __launch_bounds__(GS > 32 ? GS : 256)
+    k_delta_in(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
+  const int r = Grp<GS>::rank();
+  long long d = 0, edges = 0;
+  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
+    if (!active) return;
+    const int32_t v = list[i];
+    if (!a.M[v]) return;
+    const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
+    d += delta_in_edges<GS>(a, v, beg, end, r);
+    if (r == 0) edges += end - beg;
+  });
+  flush_block_sum(d, &a.sc->d_in);
+  flush_block_sum(edges, &a.sc->dphi_edges);
+}
+
+__global__ void __launch_bounds__(kHubThreads) k_hub_delta_in(PassArgs a) {
+  const int c = blockIdx.x;
+  const int32_t v = a.hub.vtx[a.hub.hub_of[c]];
+  if (!a.M[v]) return;  // block-uniform
+  const long long d = delta_in_edges<kHubThreads>(a, v, a.hub.e0[c], a.hub.e1[c], threadIdx.x);
+  flush_block_sum(d, &a.sc->d_in);
+  if (threadIdx.x == 0) atomicAdd((unsigned long long *)&a.sc->dphi_edges,
+                                  (unsigned long long)(a.hub.e1[c] - a.hub.e0[c]));
+}
+
+// Q = sum_x W(x)^2 - w(x)^2 over the level's ids x (W of an unused id is 0)
+// into *q (zeroed by the caller).  Unsigned arithmetic: exact whenever Q
+// fits (mu > 0 and the guard Lam T + mu V^2 < 2^60); with mu = 0 it is
+// not used.
+__global__ void k_q(PassArgs a, long long *q) {
+  long long t = 0;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.g.n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long W = (unsigned long long)a.W[x], w = (unsigned long long)a.g.vw[x];
+    t += (long long)(W * W - w * w);
+  }
+  flush_block_sum(t, q);
+}
+
+__global__ void k_save_phi_enter(PassArgs a) { a.sc->phi_enter = a.phi_acc[0]; }
+
+__global__ void k_final_phi(PassArgs a) {
+  const GraphParam P = a.gp[0];
+  const long long dq = a.sc->q_final - a.sc->q_enter;
+  a.phi_acc[0] = a.sc->phi_enter + P.Lam * a.sc->d_in - (P.mu != 0 ? P.mu * dq : 0);
+}
+
+int launch_last_pass_enter(const PassArgs &a, cudaStream_t s) {
+  cudaMemsetAsync(&a.sc->q_enter, 0, sizeof(long long), s);
+  if (a.g.n > 0) k_q<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, &a.sc->q_enter);
+  return a.g.n > 0 ? 1 : 0;
+}
+
+int launch_save_phi_enter(const PassArgs &a, cudaStream_t s) {
+  k_save_phi_enter<<<1, 1, 0, s>>>(a);
+  return 1;
+}
+
+int launch_final_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
+  cudaMemsetAsync(&a.sc->q_final, 0, sizeof(long long), s);
+  cudaMemsetAsync(&a.sc->d_in, 0, sizeof(long long), s);
+  int n = 0;
+  n += launch_vertex_kernel<1>(k_delta_in<1>, a, bin_range(b, 0, 0), s);
+  n += launch_vertex_kernel<16>(k_delta_in<16>, a, bin_range(b, 1, 1), s);
+  n += launch_vertex_kernel<32>(k_delta_in<32>, a, bin_range(b, 2, 4), s);
+  n += launch_vertex_kernel<128>(k_delta_in<128>, a, bin_range(b, 5, 6), s);
+  n += launch_vertex_kernel<512>(k_delta_in<512>, a, bin_range(b, 7, 8), s);
+  if (a.hub.H > 0) {
+    k_hub_delta_in<<<a.hub.Q, kHubThreads, 0, s>>>(a);
+    n++;
+  }
+  if (a.g.n > 0) {
+    k_q<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, &a.sc->q_final);
+    n++;
+  }
+  k_final_phi<<<1, 1, 0, s>>>(a);
+  return n + 1;
 }
 
 int launch_apply(const PassArgs &a, const ApplyScratch &w, cudaStream_t s) {

@@ -72,6 +72,14 @@ int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
 // cluster with a larger label.  size: int32[n] scratch.
 int launch_symmetry_ablation(const PassArgs &a, bool mlh, int32_t *size, cudaStream_t s);
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
+// One graph only: the objective of the state after a call's last pass
+// from the state entering it.  launch_last_pass_enter runs at the start of
+// the last pass (Q of W before its update), launch_save_phi_enter after its
+// move step (Phi it summed), launch_final_objective after its update (the
+// movers' edges, Q after; needs the pass's M and Cprev): Phi into phi_acc[0].
+int launch_last_pass_enter(const PassArgs &a, cudaStream_t s);
+int launch_save_phi_enter(const PassArgs &a, cudaStream_t s);
+int launch_final_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
 // Kept tables (Section IV-A-3): applies the last pass's moves to the tables
 // of the movers' neighbours (rebuilding any that overflow), then the argmax
 // and candidate test of Algorithm 2, read from the tables for vertices of

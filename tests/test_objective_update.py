@@ -1,0 +1,94 @@
+"""The update of the objective after a call's last pass (CPU, no GPU).
+
+The CUDA path gets Phi of the state after the last pass of a LocalMovePasses
+call from the state entering it: Eq. 1 regrouped as Phi = Lam IN - mu Q,
+with IN = sum_v S(v, C[v]) and Q = sum_X W(X)^2 - sum_v w(v)^2, and the
+moves change IN only on the movers' edges, by ([C'v = C'u] - [Cv = Cu]) w(u,v)
+per direction (an edge to a non-mover counts twice, an edge between two
+movers once from each end).  Here that rule, restated edge by edge, must
+reproduce the oracle's exact objective after every pass of every level and
+phase, for modularity, CPM and random vertex weights."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+
+def q_term(vw, C):
+    W = np.zeros(C.shape[0], dtype=object)
+    for v, x in enumerate(C):
+        W[x] += int(vw[v])
+    return sum(int(w) * int(w) for w in W) - sum(int(w) * int(w) for w in vw)
+
+
+def delta_in(rp, col, ew, C0, C1, moved):
+    d = 0
+    for v in np.nonzero(moved)[0]:
+        for e in range(rp[v], rp[v + 1]):
+            u = col[e]
+            s = int(C1[v] == C1[u]) - int(C0[v] == C0[u])
+            d += (1 if moved[u] else 2) * s * int(ew[e])
+    return d
+
+
+def graph(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(8, 60))
+    rp, col, ew = gg.random_graph(n, float(rng.uniform(0.05, 0.4)), seed, wmax=int(rng.integers(1, 6)))
+    kind = seed % 3
+    if kind == 0:
+        return gg.modularity_inputs(rp, col, ew)
+    if kind == 1:
+        return gg.cpm_inputs(rp, col, ew, 1, int(rng.integers(2, 20)))
+    vw = rng.integers(1, 6, size=n).astype(np.int64)
+    return gg.Graph(rp, col, ew, vw, int(rng.integers(1, 4)), int(rng.integers(4, 30)))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_final_objective_from_the_entering_state(seed):
+    g = graph(seed)
+    _, _, ev = oracle.louvain_plus(g, trace=True, trace_passes=True)
+    levels = {0: (g.row_ptr, g.col, g.ew, g.vw)}
+    for e in ev:
+        if e["kind"] == "contract":
+            levels[e["level"] + 1] = (e["row_ptr"], e["col"], e["ew"], e["vw"])
+    checked = 0
+    for e in ev:
+        if e["kind"] != "pass":
+            continue
+        rp, col, ew, vw = levels[e["level"]]
+        gl = gg.Graph(rp, col, ew, vw, g.lam_num, g.lam_den)
+        C0, C1, moved = e["C_before"], e["C"], e["in_M"]
+        phi0 = oracle.objective(gl, C0)
+        d_in = delta_in(rp, col, ew, C0, C1, moved)
+        dq = q_term(vw, C1) - q_term(vw, C0)
+        assert e["phi"] == phi0 + g.lam_den * d_in - g.lam_num * dq, (e["level"], e["phase"], e["pass"])
+        checked += 1
+    assert checked > 0
+
+
+def test_counting_rule_matters():
+    """Counting an edge between two movers twice (or an edge to a
+    non-mover once) breaks the identity on a pass where neighbours move
+    together, so the rule above is what the objective needs."""
+    g = graph(4)
+    _, _, ev = oracle.louvain_plus(g, trace=True, trace_passes=True)
+    wrong = 0
+    for e in ev:
+        if e["kind"] != "pass" or e["level"] != 0:
+            continue
+        C0, C1, moved = e["C_before"], e["C"], e["in_M"]
+        both = any(moved[u] for v in np.nonzero(moved)[0] for u in g.col[g.row_ptr[v]:g.row_ptr[v + 1]])
+        if not both:
+            continue
+        phi0 = oracle.objective(g, C0)
+        dq = q_term(g.vw, C1) - q_term(g.vw, C0)
+        d_twice = 0
+        for v in np.nonzero(moved)[0]:
+            for k in range(g.row_ptr[v], g.row_ptr[v + 1]):
+                u = g.col[k]
+                d_twice += 2 * (int(C1[v] == C1[u]) - int(C0[v] == C0[u])) * int(g.ew[k])
+        if e["phi"] != phi0 + g.lam_den * d_twice - g.lam_num * dq:
+            wrong += 1
+    assert wrong > 0

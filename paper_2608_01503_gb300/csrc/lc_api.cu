@@ -190,7 +190,7 @@ struct Run {
   // scratch sized for G_0
   int32_t *C = nullptr, *D = nullptr, *C_out = nullptr, *freelist = nullptr, *used = nullptr,
           *newid = nullptr, *cnt = nullptr, *scan32 = nullptr, *freepos = nullptr, *mrank = nullptr,
-          *Cprev = nullptr, *dirty = nullptr, *dirty_list = nullptr;
+          *Cprev = nullptr, *dirty = nullptr, *dirty_list = nullptr, *movers = nullptr;
   int64_t *W = nullptr, *delta = nullptr, *bound = nullptr, *off = nullptr, *scan64 = nullptr;
   uint8_t *M = nullptr, *E = nullptr;
   AbRec *ab = nullptr;
@@ -237,6 +237,7 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.freepos, n0));
   LC_TRY(r.ar.get(&r.mrank, n0));
   LC_TRY(r.ar.get(&r.Cprev, n0));
+  LC_TRY(r.ar.get(&r.movers, n0));
   if (r.o.tables == 1) {  // kept tables only
     LC_TRY(r.ar.get(&r.dirty, n0));
     LC_TRY(r.ar.get(&r.dirty_list, n0));
@@ -444,6 +445,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     a.phi_d = r.o.phi_den[i - 1];
     launch_pass_begin(r.sc, r.s);
     const bool last = i == r.o.pass_limit;
+    a.movers = incremental && last ? r.movers : nullptr;  // listed by this pass's update step
     if (incremental && last) {
       r.prof.begin(LC_K_OBJECTIVE);
       r.res->kernel_launches[LC_K_OBJECTIVE] += launch_last_pass_enter(a, r.s);

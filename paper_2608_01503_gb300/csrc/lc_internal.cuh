@@ -43,6 +43,7 @@ constexpr int64_t kBinMaxDeg[kBins - 1] = {8, 16, 32, 128, 256, 512, 1024, 2048,
 constexpr int kWarpBinWarps = 8;    // warps per block in the warp-table bins
 constexpr int kHubThreads = 256;
 constexpr int kHubChunk = 2048;     // edges per hub chunk
+constexpr int64_t kHubDeg = 4096;   // rows longer than this are hubs (bin 9)
 constexpr int kBin8Slots = 6144;    // shared table of bin 8
 constexpr int64_t kTabMinDeg = 256; // kept tables (opts.tables): vertices of degree above this
 constexpr int kUpdChunk = 256;      // edges per chunk of a mover's row in the table update
@@ -121,6 +122,8 @@ struct Scalars {
   long long q_final;     // Q after it
   long long d_in;        // change of IN by its moves
   long long dphi_edges;  // movers' edges read for d_in, summed over the call
+  int n_movers;          // entries of PassArgs::movers
+  int pad3;
 };
 
 // ------------------------------------------------------------------ hashes

@@ -1132,18 +1132,23 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_tab_scan(PassArgs a) {
 __global__ void k_apply(PassArgs a, uint8_t *__restrict__ E) {
   long long empties = 0;
   const int lane = threadIdx.x & 31;
-  // warp-uniform trip count: the chunk list below is appended per warp
+  // warp-uniform trip count: the lists below are appended per warp
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.g.n;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
-    int nch = 0;  // chunks of this mover's row for the kept tables' update
+    int nch = 0;         // chunks of this mover's row for the kept tables' update
+    bool listed = false;  // a mover for the final objective's update
     if (v < a.g.n) {
       uint8_t e = 0;
       if (a.M[v]) {
         const int32_t Dv = a.D[v], Cv = a.C[v];
         const long long wv = a.g.vw[v];
         a.Cprev[v] = Cv;
-        if (a.upd_list) nch = (int)((a.g.rp[v + 1] - a.g.rp[v] + kUpdChunk - 1) / kUpdChunk);
+        if (a.upd_list || a.movers) {
+          const int64_t deg = a.g.rp[v + 1] - a.g.rp[v];
+          if (a.upd_list) nch = (int)((deg + kUpdChunk - 1) / kUpdChunk);
+          listed = a.movers && deg <= kHubDeg;  // hubs: k_hub_delta_in
+        }
         atomicAdd((unsigned long long *)&a.W[Cv], (unsigned long long)(-wv));
         if (Dv >= 0) {
           a.C[v] = Dv;
@@ -1167,6 +1172,13 @@ __global__ void k_apply(PassArgs a, uint8_t *__restrict__ E) {
       if (lane == 31 && total > 0) first = atomicAdd(&a.sc->upd_count, total);
       first = __shfl_sync(0xFFFFFFFFu, first, 31) + incl - nch;
       for (int c = 0; c < nch; ++c) a.upd_list[first + c] = make_int2((int32_t)v, c);
+    }
+    if (a.movers) {  // uniform over the launch
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, listed);
+      int first = 0;
+      if (lane == 0 && m) first = atomicAdd(&a.sc->n_movers, __popc(m));
+      first = __shfl_sync(0xFFFFFFFFu, first, 0);
+      if (listed) a.movers[first + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
     }
   }
   __shared__ long long red[32];
@@ -1275,6 +1287,7 @@ __global__ void k_pass_begin(Scalars *sc) {
   sc->count_M = 0;
   sc->empty_movers = 0;
   sc->tab_dirty = 0;
+  sc->n_movers = 0;
   sc->upd_prev = sc->upd_count;
   sc->upd_count = 0;
 }
@@ -1616,19 +1629,18 @@ __device__ __forceinline__ long long delta_in_edges(const PassArgs &a, int32_t v
   return d;
 }
 
-template <int GS>
-__global__ void __launch_bounds__(GS > 32 ? GS : 256)
-    k_delta_in(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
-  const int r = Grp<GS>::rank();
+// dIN over the listed movers (degree <= 4096), one warp each.
+__global__ void __launch_bounds__(256) k_delta_in(PassArgs a) {
+  const int cnt = a.sc->n_movers;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   long long d = 0, edges = 0;
-  for_each_vertex<GS>(count, [&](int64_t i, bool active) {
-    if (!active) return;
-    const int32_t v = list[i];
-    if (!a.M[v]) return;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
+    const int32_t v = a.movers[j];
     const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
-    d += delta_in_edges<GS>(a, v, beg, end, r);
-    if (r == 0) edges += end - beg;
-  });
+    d += delta_in_edges<32>(a, v, beg, end, lane);
+    if (lane == 0) edges += end - beg;
+  }
   flush_block_sum(d, &a.sc->d_in);
   flush_block_sum(edges, &a.sc->dphi_edges);
 }
@@ -1679,12 +1691,8 @@ int launch_save_phi_enter(const PassArgs &a, cudaStream_t s) {
 int launch_final_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
   cudaMemsetAsync(&a.sc->q_final, 0, sizeof(long long), s);
   cudaMemsetAsync(&a.sc->d_in, 0, sizeof(long long), s);
-  int n = 0;
-  n += launch_vertex_kernel<1>(k_delta_in<1>, a, bin_range(b, 0, 0), s);
-  n += launch_vertex_kernel<16>(k_delta_in<16>, a, bin_range(b, 1, 1), s);
-  n += launch_vertex_kernel<32>(k_delta_in<32>, a, bin_range(b, 2, 4), s);
-  n += launch_vertex_kernel<128>(k_delta_in<128>, a, bin_range(b, 5, 6), s);
-  n += launch_vertex_kernel<512>(k_delta_in<512>, a, bin_range(b, 7, 8), s);
+  k_delta_in<<<152 * 8, 256, 0, s>>>(a);
+  int n = 1;
   if (a.hub.H > 0) {
     k_hub_delta_in<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     n++;

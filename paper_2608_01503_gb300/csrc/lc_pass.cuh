@@ -34,6 +34,8 @@ struct PassArgs {
   int32_t *dirty_list;       // [n] those vertices, sc->tab_dirty of them
   int2 *upd_list;            // chunks {mover, chunk} of the movers' rows, listed by the
                              // apply step when tables are kept (else nullptr)
+  int32_t *movers;           // movers of degree <= 4096, listed by the apply step of a
+                             // call's last pass (one graph; else nullptr), sc->n_movers
 };
 
 // Vertex lists of the degree bins of one level (stable: ascending ids).

@@ -501,7 +501,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   // every graph
   r.prof.begin(LC_K_OBJECTIVE);
   if (incremental) {
-    r.res->kernel_launches[LC_K_OBJECTIVE] += launch_final_objective(a, L.bins, r.s) + launch_bestof(a, r.C_out, r.s);
+    r.res->kernel_launches[LC_K_OBJECTIVE] += launch_final_objective(a, r.s) + launch_bestof(a, r.C_out, r.s);
     r.prof.end(17.0 * n);  // W, w(v) and M per vertex (+ 13 B per mover edge, added at the end)
   } else {
     r.res->kernel_launches[LC_K_OBJECTIVE] +=

@@ -1688,7 +1688,7 @@ int launch_save_phi_enter(const PassArgs &a, cudaStream_t s) {
   return 1;
 }
 
-int launch_final_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
+int launch_final_objective(const PassArgs &a, cudaStream_t s) {
   cudaMemsetAsync(&a.sc->q_final, 0, sizeof(long long), s);
   cudaMemsetAsync(&a.sc->d_in, 0, sizeof(long long), s);
   k_delta_in<<<152 * 8, 256, 0, s>>>(a);

@@ -81,7 +81,7 @@ int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
 // movers' edges, Q after; needs the pass's M and Cprev): Phi into phi_acc[0].
 int launch_last_pass_enter(const PassArgs &a, cudaStream_t s);
 int launch_save_phi_enter(const PassArgs &a, cudaStream_t s);
-int launch_final_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
+int launch_final_objective(const PassArgs &a, cudaStream_t s);
 // Kept tables (Section IV-A-3): applies the last pass's moves to the tables
 // of the movers' neighbours (rebuilding any that overflow), then the argmax
 // and candidate test of Algorithm 2, read from the tables for vertices of

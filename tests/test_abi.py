@@ -57,16 +57,19 @@ def test_struct_layouts_match_c(tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "lc.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(lc_opts), sizeof(lc_result),"
-        " sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream), offsetof(lc_result, error_detail),"
-        " sizeof(lc_server_config), offsetof(lc_server_config, opts));"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\\n\", sizeof(lc_opts),"
+        " sizeof(lc_result), sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream),"
+        " offsetof(lc_result, error_detail), sizeof(lc_server_config), offsetof(lc_server_config, opts),"
+        " offsetof(lc_opts, tables), offsetof(lc_result, kernel_bytes), offsetof(lc_result, tables_rebuilt),"
+        " (int)LC_K_COUNT);"
         "return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = list(map(int, subprocess.check_output([str(exe)]).split()))
     assert vals == [ctypes.sizeof(lc._Opts), ctypes.sizeof(lc._Result), ctypes.sizeof(lc._Event),
                     ctypes.sizeof(lc._Csr), lc._Opts.stream.offset, lc._Result.error_detail.offset,
-                    ctypes.sizeof(lc._ServerConfig), lc._ServerConfig.opts.offset]
+                    ctypes.sizeof(lc._ServerConfig), lc._ServerConfig.opts.offset, lc._Opts.tables.offset,
+                    lc._Result.kernel_bytes.offset, lc._Result.tables_rebuilt.offset, len(lc.LC_K_NAMES)]
 
 
 def test_defaults_and_strerror(lib):

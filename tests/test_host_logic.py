@@ -55,14 +55,15 @@ def test_served_recipe_mix():
 
 def test_options_marshalling():
     o = lc.Options(pass_limit=9, phi=[(1, 2)] * 9, eps=(3, 7), seed=0xFFFFFFFF + 5, uncoarsen=False,
-                   validate=False, profile=True, symmetry=2)
+                   validate=False, profile=True, symmetry=2, tables=1)
     c = lc._c_opts(o, ctypes.c_void_p(0))
+    assert c.tables == 1
     assert c.pass_limit == 9 and (c.eps_num, c.eps_den) == (3, 7)
     assert [(c.phi_num[i], c.phi_den[i]) for i in range(9)] == [(1, 2)] * 9
     assert c.seed == 4  # 32-bit salt
     assert (c.uncoarsen, c.validate, c.profile, c.symmetry) == (0, 0, 1, 2)
     d = lc._c_opts(None, ctypes.c_void_p(0))
-    assert d.pass_limit == 6 and d.symmetry == 0 and d.uncoarsen == 1
+    assert d.pass_limit == 6 and d.symmetry == 0 and d.uncoarsen == 1 and d.tables == 0
 
 
 def test_bench_percentile_helper():

@@ -16,6 +16,7 @@ Functions follow the paper's passages:
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -83,43 +84,61 @@ _CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(_Event))
 _lib = None
 
 
+def _bind(lib):
+    """Declares the C signatures on a loaded build of lc_oracle.c."""
+    G, P = ctypes.POINTER(_Graph), ctypes.POINTER(_Params)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.orc_objective.argtypes = [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, i64p,
+                                  ctypes.POINTER(ctypes.c_uint64)]
+    lib.orc_gain.argtypes = [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_int32, i64p]
+    lib.orc_local_move.argtypes = [G, P, ctypes.c_void_p, _CB, ctypes.c_void_p, i64p,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+    lib.orc_contract.argtypes = [G, ctypes.c_void_p, ctypes.c_int64, i64p, i64p,
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))]
+    lib.orc_louvain_plus.argtypes = [G, P, ctypes.c_void_p, ctypes.POINTER(_Result), _CB,
+                                     ctypes.c_void_p]
+    lib.orc_louvain_plus_constrained.argtypes = [G, P, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
+    lib.orc_louvain_plus_iterated.argtypes = [G, P, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
+    lib.orc_pleiden.argtypes = [G, P, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Result), _CB,
+                                ctypes.c_void_p]
+    lib.orc_local_move_alt.argtypes = [G, P, ctypes.c_void_p, i64p]
+    lib.orc_pleiden_refine.argtypes = [G, P, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    lib.orc_rand.argtypes = [ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+    lib.orc_rand.restype = ctypes.c_uint64
+    lib.orc_free.argtypes = [ctypes.c_void_p]
+    for f in (lib.orc_objective, lib.orc_gain, lib.orc_local_move, lib.orc_contract,
+              lib.orc_louvain_plus, lib.orc_louvain_plus_constrained,
+              lib.orc_louvain_plus_iterated, lib.orc_pleiden, lib.orc_local_move_alt,
+              lib.orc_pleiden_refine):
+        f.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        G, P = ctypes.POINTER(_Graph), ctypes.POINTER(_Params)
-        i64p = ctypes.POINTER(ctypes.c_int64)
-        lib.orc_objective.argtypes = [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, i64p,
-                                      ctypes.POINTER(ctypes.c_uint64)]
-        lib.orc_gain.argtypes = [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
-                                 ctypes.c_int32, i64p]
-        lib.orc_local_move.argtypes = [G, P, ctypes.c_void_p, _CB, ctypes.c_void_p, i64p,
-                                       ctypes.POINTER(ctypes.c_uint64)]
-        lib.orc_contract.argtypes = [G, ctypes.c_void_p, ctypes.c_int64, i64p, i64p,
-                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
-                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
-                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
-                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))]
-        lib.orc_louvain_plus.argtypes = [G, P, ctypes.c_void_p, ctypes.POINTER(_Result), _CB,
-                                         ctypes.c_void_p]
-        lib.orc_louvain_plus_constrained.argtypes = [G, P, ctypes.c_void_p, ctypes.c_void_p,
-                                                     ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
-        lib.orc_louvain_plus_iterated.argtypes = [G, P, ctypes.c_int32, ctypes.c_void_p,
-                                                  ctypes.POINTER(_Result), _CB, ctypes.c_void_p]
-        lib.orc_pleiden.argtypes = [G, P, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Result), _CB,
-                                    ctypes.c_void_p]
-        lib.orc_local_move_alt.argtypes = [G, P, ctypes.c_void_p, i64p]
-        lib.orc_pleiden_refine.argtypes = [G, P, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
-        lib.orc_rand.argtypes = [ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
-        lib.orc_rand.restype = ctypes.c_uint64
-        lib.orc_free.argtypes = [ctypes.c_void_p]
-        for f in (lib.orc_objective, lib.orc_gain, lib.orc_local_move, lib.orc_contract,
-                  lib.orc_louvain_plus, lib.orc_louvain_plus_constrained,
-                  lib.orc_louvain_plus_iterated, lib.orc_pleiden, lib.orc_local_move_alt,
-                  lib.orc_pleiden_refine):
-            f.restype = ctypes.c_int
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Runs every oracle function against another build of lc_oracle.c while
+    the context is open.  The tests compile copies with planted mistakes and
+    check that the pins reject them."""
+    global _lib
+    saved = _lib
+    _lib = _bind(ctypes.CDLL(os.path.abspath(path)))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 @dataclass

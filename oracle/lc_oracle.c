@@ -32,6 +32,10 @@
  * re-evaluation; contraction against a membership-matrix product and the
  * constant objective offset; whole runs against exhaustive search, lambda=0
  * components, networkx modularity and hand-derived closed forms.
+ * Algorithm 1's coarsening stop (|C_l| = |V_l|) and the ascending-id label
+ * compaction are pinned in tests/test_oracle_coarsening.py by re-running the
+ * pinned LocalMovePasses on every traced level and by sparse membership
+ * products, with planted early and late stops rejected.
  * Parity unpinned (readings, no passage fixes them): the hash salt and the
  * bucket rounding of the ordering, and which free ids the empty-cluster
  * movers receive; they are pinned only through GPU/oracle bit-exactness.

@@ -36,8 +36,13 @@
  *    after the call returns.  Work is issued on opts->stream (NULL = the
  *    legacy default stream); every call returns after its results are
  *    complete on that stream (calls read per-level sizes back to the host).
- *  - Scratch device memory is taken from CUDA's stream-ordered allocator
- *    (cudaMallocAsync on opts->stream) and released before return.
+ *  - Scratch device memory comes from opts->alloc / opts->dealloc when the
+ *    caller sets them (the Python binding passes PyTorch's caching
+ *    allocator), else from a stream-ordered memory pool private to the
+ *    library (cudaMemPoolCreate; the device's default pool is never
+ *    touched).  Either way every scratch buffer is returned before the call
+ *    returns: to the caller's allocator, or to the private pool, which keeps
+ *    the freed blocks cached for later calls until lc_release_memory().
  *  - Return value: LC_OK or an LC_ERR_* code; on error no output is
  *    guaranteed to have been written (labels_out may hold partial data) and
  *    *res is zeroed except for res->error_detail.  lc_strerror() names it.
@@ -49,6 +54,7 @@
 #ifndef LC_H
 #define LC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -106,6 +112,18 @@ typedef struct {
 } lc_event;
 typedef void (*lc_event_fn)(void *ctx, const lc_event *ev);
 
+/* Device memory provider of lc_opts (optional; both or neither).
+ * alloc returns `bytes` of device memory on the current device that may be
+ * used in the order of `stream` (the cudaStream_t of the call), or NULL if
+ * it has none, which fails the call with LC_ERR_OOM after everything it
+ * took is given back.  dealloc returns a block in the order of the same
+ * stream; the library calls it once per block, before the call that took
+ * the block returns.  ctx is lc_opts.alloc_ctx.  Server slots call these
+ * from their own threads, so a provider given to lc_server_create must be
+ * thread-safe. */
+typedef void *(*lc_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*lc_free_fn)(void *ctx, void *ptr, size_t bytes, void *stream);
+
 /* Options.  Initialise with lc_default_opts(). */
 typedef struct {
   int32_t pass_limit;       /* passes per LocalMovePasses call (Algorithm 2); default 6, max 16 */
@@ -134,6 +152,10 @@ typedef struct {
   int64_t scratch_limit;    /* bytes of device scratch one call may hold at once; 0 = no
                                limit.  A call that needs more returns LC_ERR_OOM (nothing
                                is kept allocated), as when the device itself runs out. */
+  lc_alloc_fn alloc;        /* device scratch provider (see lc_alloc_fn); NULL together
+                               with dealloc = the library's private pool (default) */
+  lc_free_fn dealloc;
+  void *alloc_ctx;          /* passed to alloc and dealloc */
 } lc_opts;
 
 /* Kernel classes timed when opts.profile = 1. */
@@ -171,14 +193,31 @@ typedef struct {
   int64_t error_detail; /* extra context for some errors (e.g. offending vertex) */
   int64_t tables_rebuilt; /* kept tables (opts.tables) that ran out of slots during an
                              in-place update and were rebuilt from the labels */
+  int64_t scratch_peak_bytes; /* most device scratch the call held at once (bytes
+                                 requested from the provider) */
 } lc_result;
 
 /* Fill *o with the defaults of Section VI-C (pass limit 6, phi 3/4 x4 then
  * 1/4 x2, epsilon 1/10, seed 0, Louvain+, validate on, profile off). */
 LC_API void lc_default_opts(lc_opts *o);
 
+/* Upper estimate, in bytes, of the device scratch lc_cluster (count = 1) or
+ * lc_cluster_batch (count graphs) needs on a graph of n vertices and nnz
+ * stored edges: the level-0 scratch exactly, the sizes the driver requests,
+ * plus coarse levels whose vertex and edge counts sum to at most those of
+ * the input.  A run whose levels shrink more slowly can need more (compare
+ * lc_result.scratch_peak_bytes).  -1 for negative sizes or count < 1. */
+LC_API int64_t lc_scratch_estimate(int64_t n, int64_t nnz, int32_t count, const lc_opts *opts);
+
 /* Human-readable name of an LC_* code (static string). */
 LC_API const char *lc_strerror(int code);
+
+/* Returns the blocks cached in the library's private memory pool on the
+ * current device to the device (cudaMemPoolTrimTo after a device-wide
+ * synchronize), e.g. before handing the GPU's memory to another allocator.
+ * Later calls grow the pool again.  Memory that opts.alloc provided is never
+ * cached by the library.  LC_OK or LC_ERR_CUDA. */
+LC_API int lc_release_memory(void);
 
 /* Louvain+ (Algorithm 1) on G = (g, vertex_w, edge_w) with
  * lambda = lambda_num / lambda_den.  labels_out: device int32[n], written
@@ -247,15 +286,21 @@ LC_API int lc_cluster_batch(const lc_csr *g, const int64_t *vertex_w, const int3
 /* Clustering service (the served form).  Requests are host graphs; the
  * server copies them on submit.  `slots` worker threads, each with its own
  * CUDA stream on the device that was current at lc_server_create, admit
- * queued requests in arrival order while their estimated device footprint
- * (24 bytes per stored edge + 120 bytes per vertex + 1 MiB) fits in the
+ * queued requests in arrival order while their device footprint fits in the
  * unclaimed part of `hbm_budget` (0: half of the free device memory at
  * creation; a request larger than the whole budget runs alone), up to
  * `max_batch` per slot, and cluster each admission as one
- * lc_cluster_batch call.  Slots run concurrently, so requests arriving while
- * others are on the GPU start as soon as a slot and memory free up.  Every
- * job's labels and result equal lc_cluster's for that graph alone.  opts
- * applies to every job (its stream, trace and profile fields are ignored). */
+ * lc_cluster_batch call.  A request's footprint is its packed input (24
+ * bytes per vertex + 8 per stored edge) plus lc_scratch_estimate() for it;
+ * an admission's clustering runs with the scratch it reserved as its
+ * scratch limit, and if the estimate falls short its requests return to the
+ * head of the queue with twice the reservation (LC_ERR_OOM reaches a caller
+ * only when the device itself is out of memory).  Slots run concurrently,
+ * so requests arriving while others are on the GPU start as soon as a slot
+ * and memory free up.  Every job's labels and result equal lc_cluster's for
+ * that graph alone.  opts applies to every job (its stream, trace, profile
+ * and scratch_limit fields are ignored; its allocator, if set, is called
+ * from the slots' threads). */
 typedef struct lc_server lc_server;
 typedef struct {
   int32_t slots;      /* concurrent admissions (default 4, max 64) */
@@ -338,8 +383,10 @@ LC_API int lc_objective(const lc_csr *g, const int64_t *vertex_w, const int32_t 
  * first call before any stream capture.  Every call shares the array and
  * clears the parts that must start at zero; calls whose work overlaps on
  * the GPU (e.g. issued on different streams without ordering) race on it.
- * The CSR preconditions are not validated; labels outside [0, n) give
- * LC_ERR_ARG; inputs beyond the exactness guards give LC_ERR_OVERFLOW.
+ * The CSR is checked only as far as the sweep's reads need: row_ptr[0] = 0,
+ * row_ptr[n] = nnz, every row inside [0, nnz] and column indices in [0, n),
+ * else LC_ERR_ARG (symmetry, sortedness and weights are not validated).  Labels outside [0, n) give LC_ERR_ARG; inputs beyond the
+ * exactness guards give LC_ERR_OVERFLOW.
  * Work is issued on opts->stream (opts may be NULL) and the call returns
  * after the result is on the host. */
 LC_API int lc_objective_static(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,

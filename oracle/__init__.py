@@ -20,6 +20,7 @@ import contextlib
 import ctypes
 import os
 import subprocess
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -120,11 +121,15 @@ def _bind(lib):
     return lib
 
 
+_load_lock = threading.Lock()
+
+
 def _load():
     global _lib
-    if _lib is None:
-        _lib = _bind(ctypes.CDLL(build()))
-    return _lib
+    with _load_lock:  # threads (louvain_plus_many) may arrive together
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+        return _lib
 
 
 @contextlib.contextmanager
@@ -292,6 +297,26 @@ def louvain_plus(g, params: Params | None = None, trace: bool = False, trace_pas
     events hold every LocalMovePasses result and coarse graph; trace_passes
     adds every pass's intermediate state."""
     return _run(g, params, trace, trace_passes, "louvain_plus")
+
+
+def louvain_plus_many(graphs, params: Params | None = None, threads: int | None = None):
+    """louvain_plus on every graph (no trace), the graphs spread over host
+    threads: the C calls release the GIL and share nothing, so each result
+    is what one call alone returns.  Returns [(labels, result dict)]."""
+    import concurrent.futures as cf
+
+    def one(g):
+        labels, res, _ = louvain_plus(g, params)
+        return labels, res
+
+    _load()
+    # largest first, so the long runs do not start last
+    order = sorted(range(len(graphs)), key=lambda k: -graphs[k].nnz)
+    out = [None] * len(graphs)
+    with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
+        for k, r in zip(order, ex.map(one, [graphs[k] for k in order])):
+            out[k] = r
+    return out
 
 
 def louvain_plus_constrained(g, constraint, params: Params | None = None, trace: bool = False,

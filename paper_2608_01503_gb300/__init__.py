@@ -2,8 +2,10 @@
 
 Argument marshalling only: every step of the method runs in the CUDA kernels
 of ``liblc.so`` behind the C ABI declared in ``include/lc.h``.  PyTorch
-provides device memory and the current CUDA stream.  If the native library
-is missing or cannot be loaded, every call raises; there is no CPU path.
+provides device memory (its caching allocator is passed to the library as
+the scratch provider, ``Options.allocator = "torch"``, the default) and the
+current CUDA stream.  If the native library is missing or cannot be loaded,
+every call raises; there is no CPU path.
 
 Functions carry the C names:
   lc_cluster        Louvain+ (Algorithm 1) on device tensors
@@ -18,6 +20,8 @@ Functions carry the C names:
   lc_objective_static  the same without allocating device memory
   lc_server_*       the clustering service: submit host graphs, poll/wait
                     for results; Server wraps it as a context manager
+  lc_scratch_estimate  device scratch a call is expected to need
+  lc_release_memory    return the library pool's cached blocks to the device
   lc_strerror       name of an error code
 """
 from __future__ import annotations
@@ -62,6 +66,29 @@ class _Event(ctypes.Structure):
 
 
 _EventFn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(_Event))
+_AllocFn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FreeFn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+def _torch_alloc(_ctx, nbytes, stream):
+    """lc_alloc_fn over PyTorch's caching allocator, on the call's stream."""
+    import torch
+
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except RuntimeError:  # out of memory: the call returns LC_ERR_OOM
+        return None
+
+
+def _torch_free(_ctx, ptr, _nbytes, _stream):
+    import torch
+
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+# module-level, so the C function pointers outlive every call
+_TORCH_ALLOC = _AllocFn(_torch_alloc)
+_TORCH_FREE = _FreeFn(_torch_free)
 
 
 class _Opts(ctypes.Structure):
@@ -72,7 +99,8 @@ class _Opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p),
                 ("symmetry", ctypes.c_int32), ("tables", ctypes.c_int32),
-                ("scratch_limit", ctypes.c_int64)]
+                ("scratch_limit", ctypes.c_int64), ("alloc", _AllocFn), ("dealloc", _FreeFn),
+                ("alloc_ctx", ctypes.c_void_p)]
 
 
 class _Result(ctypes.Structure):
@@ -82,7 +110,8 @@ class _Result(ctypes.Structure):
                 ("modularity", ctypes.c_double), ("edges_local_move", ctypes.c_int64),
                 ("edges_contract", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 10),
                 ("kernel_launches", ctypes.c_int64 * 10), ("kernel_bytes", ctypes.c_double * 10),
-                ("error_detail", ctypes.c_int64), ("tables_rebuilt", ctypes.c_int64)]
+                ("error_detail", ctypes.c_int64), ("tables_rebuilt", ctypes.c_int64),
+                ("scratch_peak_bytes", ctypes.c_int64)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -95,7 +124,8 @@ EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "
            "lc_cluster_constrained", "lc_cluster_iterated", "lc_cluster_leiden",
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
            "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
-           "lc_server_wait", "lc_server_destroy", "lc_server_cancel"]
+           "lc_server_wait", "lc_server_destroy", "lc_server_cancel", "lc_release_memory",
+           "lc_scratch_estimate"]
 
 
 def library_path() -> str:
@@ -132,6 +162,10 @@ def load(build_if_missing: bool = True):
     lib.lc_objective_static.argtypes = [csr, P, P, i64, i64, P, opts, res]
     lib.lc_objective_static_max_vertices.argtypes = []
     lib.lc_objective_static_max_vertices.restype = ctypes.c_int64
+    lib.lc_release_memory.argtypes = []
+    lib.lc_release_memory.restype = ctypes.c_int
+    lib.lc_scratch_estimate.argtypes = [i64, i64, i32, opts]
+    lib.lc_scratch_estimate.restype = ctypes.c_int64
     srv = ctypes.c_void_p
     lib.lc_server_default_config.argtypes = [ctypes.POINTER(_ServerConfig)]
     lib.lc_server_default_config.restype = None
@@ -169,10 +203,14 @@ class Options:
     symmetry: int = 0  # 0 afterburner, 1 none, 2 minimum label heuristic in odd passes
     scratch_limit: int = 0  # bytes of device scratch a call may hold; 0 = no limit
     tables: int = 0  # 1: high-degree tables kept across passes and updated in place
+    allocator: str = "torch"  # device scratch from PyTorch's caching allocator, or "library"
+                              # for liblc's private pool
 
 
 def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     o = o or Options()
+    if o.allocator not in ("torch", "library"):
+        raise ValueError(f"allocator must be 'torch' or 'library', not {o.allocator!r}")
     c = _Opts()
     load().lc_default_opts(ctypes.byref(c))
     c.pass_limit = o.pass_limit
@@ -190,6 +228,9 @@ def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     c.stream = stream
     if event_fn is not None:
         c.event_cb = event_fn
+    if o.allocator == "torch":
+        c.alloc = _TORCH_ALLOC
+        c.dealloc = _TORCH_FREE
     return c
 
 
@@ -216,7 +257,7 @@ def _dev(t, dtype, name):
 def _result(r: _Result) -> dict:
     out = {k: getattr(r, k) for k in ("n_clusters", "levels", "passes_total", "phi", "lambda_den",
                                       "objective", "modularity", "edges_local_move", "edges_contract",
-                                      "error_detail", "tables_rebuilt")}
+                                      "error_detail", "tables_rebuilt", "scratch_peak_bytes")}
     out["kernel_ms"] = dict(zip(LC_K_NAMES, list(r.kernel_ms)))
     out["kernel_launches"] = dict(zip(LC_K_NAMES, list(r.kernel_launches)))
     out["kernel_bytes"] = dict(zip(LC_K_NAMES, list(r.kernel_bytes)))
@@ -452,6 +493,18 @@ def lc_objective(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, labels,
     return _result(res)
 
 
+def lc_scratch_estimate(n: int, nnz: int, count: int = 1, opts: Options | None = None) -> int:
+    """Upper estimate of the device scratch lc_cluster (count = 1) or
+    lc_cluster_batch needs for n vertices and nnz stored edges (bytes)."""
+    c = _c_opts(opts, None)
+    return int(load().lc_scratch_estimate(int(n), int(nnz), int(count), ctypes.byref(c)))
+
+
+def lc_release_memory() -> None:
+    """Returns the blocks cached in liblc's private pool on the current device."""
+    _check(load().lc_release_memory())
+
+
 def lc_objective_static_max_vertices() -> int:
     return int(load().lc_objective_static_max_vertices())
 
@@ -468,7 +521,7 @@ def lc_objective_static(row_ptr, col, ew, vw, lambda_num: int, lambda_den: int, 
     lib = load()
     n = row_ptr.numel() - 1
     csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
-    c = _c_opts(None, _stream_handle(stream))
+    c = _c_opts(Options(allocator="library"), _stream_handle(stream))  # it allocates nothing
     res = _Result()
     rc = lib.lc_objective_static(ctypes.byref(csr), _dev(vw, torch.int64, "vw"),
                                  _dev(ew, torch.int32, "ew"), int(lambda_num), int(lambda_den),
@@ -489,7 +542,8 @@ def lc_server_create(slots: int = 4, max_batch: int = 64, hbm_budget: int = 0,
     """Starts a clustering service on the current device; returns its handle."""
     cfg = lc_server_default_config()
     cfg.slots, cfg.max_batch, cfg.hbm_budget = slots, max_batch, hbm_budget
-    cfg.opts = _c_opts(opts, None)
+    # the slots' own threads allocate; the library's pool unless asked otherwise
+    cfg.opts = _c_opts(opts or Options(allocator="library"), None)
     h = ctypes.c_void_p()
     _check(load().lc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h

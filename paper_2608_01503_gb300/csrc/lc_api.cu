@@ -5,9 +5,11 @@
 // new-singleton bookkeeping run on the device.  Per level the host reads the
 // bin sizes, the cluster count n_c and the coarse edge count, which size the
 // launches and the coarse graph G_{l+1}.  All scratch memory comes from the
-// stream-ordered allocator and is sized once for G_0 and reused by every
-// coarser level (Section IV-C-1, memory reuse); only coarse graphs are
-// allocated per level.
+// call's provider (lc_memory.cuh: the caller's allocator or the library's
+// private pool) and is sized once for G_0 and reused by every coarser level
+// (Section IV-C-1, memory reuse); only coarse graphs are allocated per
+// level.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +20,7 @@
 #include "lc_contract.cuh"
 #include "lc_leiden.cuh"
 #include "lc_internal.cuh"
+#include "lc_memory.cuh"
 #include "lc_pass.cuh"
 #include "lc_scan.cuh"
 #include "lc_validate.cuh"
@@ -51,52 +54,11 @@ static int launch_check() {
   return LC_OK;
 }
 
-// ------------------------------------------------------------- memory
-
-// Stream-ordered device allocations released together at scope exit.
-struct Arena {
-  cudaStream_t s;
-  std::vector<void *> ptrs;
-  std::vector<size_t> sizes;
-  int64_t limit = 0, held = 0;  // opts.scratch_limit (0 = none) and bytes held
-  explicit Arena(cudaStream_t st) : s(st) {}
-  Arena(const Arena &) = delete;
-  ~Arena() {
-    for (void *p : ptrs) cudaFreeAsync(p, s);
-  }
-  template <class T>
-  int get(T **out, int64_t count) {
-    void *p = nullptr;
-    const size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
-    if (limit > 0 && held + (int64_t)bytes > limit) {
-      *out = nullptr;
-      return LC_ERR_OOM;
-    }
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      *out = nullptr;
-      return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
-    }
-    ptrs.push_back(p);
-    sizes.push_back(bytes);
-    held += (int64_t)bytes;
-    *out = (T *)p;
-    return LC_OK;
-  }
-  void release(void *p) {
-    for (size_t i = 0; i < ptrs.size(); ++i)
-      if (ptrs[i] == p) {
-        cudaFreeAsync(p, s);
-        ptrs[i] = nullptr;
-        held -= (int64_t)sizes[i];
-      }
-  }
-};
+// ------------------------------------------------------------- device
 
 // Once per device; several host threads (the server's slots) may get here
 // together, so the flag is set only after the configuration is in place.
-static void keep_pool_memory() {
+static void configure_device() {
   static std::mutex mtx;
   static uint64_t done_mask = 0;
   int dev = 0;
@@ -104,14 +66,9 @@ static void keep_pool_memory() {
   const uint64_t bit = dev < 64 ? (1ull << dev) : 0;
   std::lock_guard<std::mutex> lock(mtx);
   if (done_mask & bit) return;
-  done_mask |= bit;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
   configure_kernels();
   cudaGetLastError();
+  done_mask |= bit;
 }
 
 // ------------------------------------------------------------ profile
@@ -206,7 +163,7 @@ struct Run {
   uint8_t *keep = nullptr;
   GraphStats *st = nullptr;
   std::vector<long long> hT, hV, hsw2;
-  explicit Run(cudaStream_t st_) : s(st_), ar(st_) {}
+  explicit Run(const lc_opts &o_) : s((cudaStream_t)o_.stream), o(o_), ar((cudaStream_t)o_.stream, o_) {}
 };
 
 static int alloc_per_graph(Run &r) {
@@ -260,6 +217,35 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_CK(cudaMemsetAsync(r.gtab, 0, sizeof(unsigned long long) * (size_t)(2 * nnz0 > 0 ? 2 * nnz0 : 1), r.s));
   LC_CK(cudaMemsetAsync(r.sc, 0, sizeof(Scalars), r.s));
   return LC_OK;
+}
+
+// Bytes the allocations above, prepare() and level0() request for G_0 of a
+// call on `G` graphs (kept in step with them), and those of one level's
+// bins, hub plan, parameters, dense ids and coarse graph (bins_for,
+// upload_params, compact_level, contract_level), for the footprint below.
+static int64_t level0_scratch_bytes(int64_t n0, int64_t nnz0, int64_t G, int tables) {
+  const int64_t n = n0 > 0 ? n0 : 1, big = 2 * nnz0 > n0 + 1 ? 2 * nnz0 : n0 + 1;
+  int64_t b = G * (6 * 8 + 4 + 4 + 1);                      // alloc_per_graph
+  b += 11 * 4 * n;                                           // C .. movers
+  if (tables == 1) b += 2 * 4 * n + 8 * upd_list_size(n0, nnz0);
+  b += 4 * scan_scratch(big);                                // scan32
+  b += 3 * 8 * n + (int64_t)sizeof(AbRec) * n;               // W, delta, ab (and bound, off below)
+  b += 2 * 8 * (n0 + 1) + 8 * scan_scratch(n0 + 1) + 2 * n;  // bound, off, scan64, M, E
+  b += 8 * (2 * nnz0 > 0 ? 2 * nnz0 : 1);                    // gtab
+  if (G > 1) b += 8 * n + 8 * (G + 1) + 4 * n;               // gself, graph_ptr, gid
+  return b + (int64_t)sizeof(Scalars) + (int64_t)sizeof(GraphStats);
+}
+static int64_t level_bytes(int64_t n, int64_t nnz, int64_t G) {
+  const int64_t hubs = nnz / kHubDeg + 1, chunks = nnz / kHubChunk + hubs;
+  return 4 * n + 4 * (kBins + 1) + 40 * chunks + 36 * hubs  // bins, hub plan
+         + (int64_t)sizeof(GraphParam) * G                   // upload_params
+         + 4 * n + (G > 1 ? 4 * n : 0)                      // Cd, next level's gid
+         + 16 * (n + 1) + 8 * nnz;                          // coarse row_ptr, vw, col, ew
+}
+
+int64_t cluster_footprint(int64_t n, int64_t nnz, int count, const lc_opts &o) {
+  // level 0 exactly, then coarse levels whose sizes sum to at most G_0's
+  return level0_scratch_bytes(n, nnz, count, o.tables) + 2 * level_bytes(n, nnz, count) + (1 << 20);
 }
 
 // Degree bins of a level, and the chunk plan of its hub bin (rows longer
@@ -702,6 +688,7 @@ static int check_opts(const lc_opts &o) {
   if (o.symmetry < 0 || o.symmetry > 2) return LC_ERR_ARG;
   if (o.tables < 0 || o.tables > 1) return LC_ERR_ARG;
   if (o.scratch_limit < 0) return LC_ERR_ARG;
+  if ((o.alloc == nullptr) != (o.dealloc == nullptr)) return LC_ERR_ARG;
   return LC_OK;
 }
 
@@ -918,7 +905,7 @@ static int begin_call(Run &r, const lc_opts *opts, lc_result *res, int G) {
   memset(res, 0, sizeof(lc_result) * (size_t)G);
   LC_TRY(check_opts(r.o));
   r.ar.limit = r.o.scratch_limit;
-  keep_pool_memory();
+  configure_device();
   r.prof.on = r.o.profile != 0;
   r.prof.s = r.s;
   fill_method(r);
@@ -958,6 +945,8 @@ static void end_call(Run &r, int rc) {
     int64_t detail = r.res->error_detail;
     memset(r.res, 0, sizeof(lc_result) * (size_t)r.G);
     r.res->error_detail = detail;
+  } else {
+    r.res->scratch_peak_bytes = r.ar.peak;
   }
 }
 
@@ -1152,6 +1141,11 @@ void lc_default_opts(lc_opts *o) {
   o->event_ctx = nullptr;
 }
 
+int64_t lc_scratch_estimate(int64_t n, int64_t nnz, int32_t count, const lc_opts *opts) {
+  if (n < 0 || nnz < 0 || count < 1) return -1;
+  return cluster_footprint(n, nnz, count, resolve_opts(opts));
+}
+
 const char *lc_strerror(int code) {
   switch (code) {
     case LC_OK: return "ok";
@@ -1179,7 +1173,7 @@ static int cluster_single(const lc_csr *g, const int64_t *vertex_w, const int32_
                           const lc_opts *opts, int32_t *labels_out, lc_result *res) {
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
-  Run r((cudaStream_t)o.stream);
+  Run r(o);
   int rc = begin_call(r, opts, res, 1);
   if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
   if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
@@ -1220,7 +1214,7 @@ int lc_cluster_leiden(const lc_csr *g, const int64_t *vertex_w, const int32_t *e
                       int32_t *labels_out, lc_result *res) {
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
-  Run r((cudaStream_t)o.stream);
+  Run r(o);
   int rc = begin_call(r, opts, res, 1);
   if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
   if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
@@ -1248,10 +1242,11 @@ int lc_cluster_iterated(const lc_csr *g, const int64_t *vertex_w, const int32_t 
   const lc_opts o = resolve_opts(opts);
   const cudaStream_t s = (cudaStream_t)o.stream;
   int32_t *B = nullptr;
-  if (cudaMallocAsync(&B, sizeof(int32_t) * (size_t)g->n, s) != cudaSuccess) {
-    cudaGetLastError();
+  const size_t b_bytes = sizeof(int32_t) * (size_t)g->n;
+  rc = dev_alloc(o, s, b_bytes, (void **)&B);
+  if (rc != LC_OK) {
     memset(res, 0, sizeof(*res));
-    return LC_ERR_OOM;
+    return rc;
   }
   lc_result total = *res;
   for (int32_t it = 1; it < iterations && rc == LC_OK; ++it) {
@@ -1268,6 +1263,7 @@ int lc_cluster_iterated(const lc_csr *g, const int64_t *vertex_w, const int32_t 
     }
     const lc_result prev = total;
     total = ri;  // clusters, levels and objective of the last iteration
+    total.scratch_peak_bytes = std::max(ri.scratch_peak_bytes, prev.scratch_peak_bytes);
     total.passes_total += prev.passes_total;
     total.edges_local_move += prev.edges_local_move;
     total.edges_contract += prev.edges_contract;
@@ -1277,8 +1273,9 @@ int lc_cluster_iterated(const lc_csr *g, const int64_t *vertex_w, const int32_t 
       total.kernel_bytes[k] += prev.kernel_bytes[k];
     }
   }
-  cudaFreeAsync(B, s);
+  dev_free(o, s, B, b_bytes);
   if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
+  total.scratch_peak_bytes += (int64_t)b_bytes;  // the constraint, held across the later runs
   *res = total;
   if (rc != LC_OK) {
     const int64_t detail = res->error_detail;
@@ -1293,7 +1290,7 @@ int lc_cluster_batch(const lc_csr *g, const int64_t *vertex_w, const int32_t *ed
                      const lc_opts *opts, int32_t *labels_out, lc_result *res) {
   if (!res || count < 1 || !graph_ptr || !lambda_num || !lambda_den) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
-  Run r((cudaStream_t)o.stream);
+  Run r(o);
   int rc = begin_call(r, opts, res, count);
   if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
   std::vector<int64_t> gptr(graph_ptr, graph_ptr + count + 1);
@@ -1324,8 +1321,9 @@ int lc_cluster_host(const lc_csr *g, const int64_t *vertex_w, const int32_t *edg
   if (rc != LC_OK) return rc;
   if (g->n > 0 && !labels_out) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
+  if (check_opts(o) != LC_OK) return LC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)o.stream;
-  Arena ar(s);
+  Arena ar(s, o);
   int64_t *d_rp = nullptr, *d_vw = nullptr;
   int32_t *d_col = nullptr, *d_ew = nullptr, *d_lab = nullptr;
   const int64_t n = g->n, nnz = g->nnz;
@@ -1356,7 +1354,7 @@ int lc_local_move(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_
                   int32_t *labels_inout, int32_t singleton_start, lc_result *res) {
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
-  Run r((cudaStream_t)o.stream);
+  Run r(o);
   int rc = begin_call(r, opts, res, 1);
   if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
   if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);
@@ -1404,7 +1402,7 @@ int lc_contract(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w,
   if (g->n > 0 && n_c == 0) return LC_ERR_ARG;
   lc_result tmp;
   lc_opts o = resolve_opts(opts);
-  Run r((cudaStream_t)o.stream);
+  Run r(o);
   rc = begin_call(r, opts, &tmp, 1);
   if (rc != LC_OK) return rc;
   *c_nnz = 0;
@@ -1448,7 +1446,7 @@ int lc_objective(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w
                  const lc_opts *opts, lc_result *res) {
   if (!res) return LC_ERR_ARG;
   lc_opts o = resolve_opts(opts);
-  Run r((cudaStream_t)o.stream);
+  Run r(o);
   int rc = begin_call(r, opts, res, 1);
   if (rc == LC_OK) rc = check_graph_args(g, vertex_w, edge_w);
   if (rc == LC_OK) rc = check_lambda(lambda_num, lambda_den);

@@ -46,6 +46,7 @@ struct Acc {
   unsigned long long sw2;       // sum of w(v)^2
   unsigned long long clusters;  // labels in use
   unsigned long long bad_label; // labels outside [0, n)
+  unsigned long long bad_col;   // rows outside [0, nnz] and columns outside [0, n) (not followed)
 };
 
 struct View {
@@ -104,7 +105,7 @@ __global__ void k_static_weights(void *base, const int32_t *__restrict__ C,
 }
 
 // One warp per vertex: S(v, C[v]) over the row, then Lambda*w'(v, C[v]).
-__global__ void k_static_sweep(void *base, int64_t n, const int64_t *__restrict__ rp,
+__global__ void k_static_sweep(void *base, int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
                                const int32_t *__restrict__ col, const int32_t *__restrict__ ew,
                                const int64_t *__restrict__ vw, const int32_t *__restrict__ C,
                                long long mu, long long Lam) {
@@ -112,14 +113,23 @@ __global__ void k_static_sweep(void *base, int64_t n, const int64_t *__restrict_
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long phi = 0, T = 0, used = 0;
+  unsigned long long phi = 0, T = 0, used = 0, bad = 0;
   for (int64_t v = warp; v < n; v += nw) {
     const int32_t x = C[v];
     const bool ok = x >= 0 && x < n;
     long long self = 0, t = 0;
-    for (int64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+    int64_t rb = rp[v], re = rp[v + 1];
+    if (rb < 0 || rb > re || re > nnz) {  // a malformed row: counted, never read
+      if (lane == 0) bad++;
+      rb = re = 0;
+    }
+    for (int64_t e = rb + lane; e < re; e += 32) {
       const int32_t u = col[e];
       t += ew[e];
+      if (u < 0 || u >= n) {  // a malformed CSR: counted, never dereferenced
+        bad++;
+        continue;
+      }
       if (ok && C[u] == x) self += ew[e];
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -140,6 +150,7 @@ __global__ void k_static_sweep(void *base, int64_t n, const int64_t *__restrict_
     atomicAdd(&s.acc->T, T);
     if (used) atomicAdd(&s.acc->clusters, used);
   }
+  if (bad) atomicAdd(&s.acc->bad_col, bad);
 }
 
 std::mutex g_mu;
@@ -197,16 +208,27 @@ LC_API int lc_objective_static(const lc_csr *g, const int64_t *vertex_w, const i
   int rc = static_base(&base);
   if (rc != LC_OK) return rc;
   const int64_t n = g->n;
+  cudaGetLastError();  // an earlier, unrelated launch error is not this call's
+  // the row structure bounds every read of the sweep: row_ptr[0] = 0 and
+  // row_ptr[n] = nnz (two 8-byte reads into the host stack, no allocation)
+  int64_t ends[2] = {-1, -1};
+  if (cudaMemcpyAsync(&ends[0], g->row_ptr, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&ends[1], g->row_ptr + n, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LC_ERR_CUDA;
+  }
+  if (ends[0] != 0 || ends[1] != g->nnz) return LC_ERR_ARG;
   k_static_clear<<<blocks_for(n, 256), 256, 0, s>>>(base, n);
   k_static_weights<<<blocks_for(n, 256), 256, 0, s>>>(base, labels, vertex_w, n);
-  k_static_sweep<<<blocks_for(n * 32, 256), 256, 0, s>>>(base, n, g->row_ptr, g->col, edge_w, vertex_w,
+  k_static_sweep<<<blocks_for(n * 32, 256), 256, 0, s>>>(base, n, g->nnz, g->row_ptr, g->col, edge_w, vertex_w,
                                                           labels, lambda_num, lambda_den);
   Acc acc;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(&acc, view_of(base).acc, sizeof(acc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return LC_ERR_CUDA;
-  if (acc.bad_label) return LC_ERR_ARG;
+  if (acc.bad_label || acc.bad_col) return LC_ERR_ARG;
   // the sums are exact under the library's guards; beyond them, refuse
   const __int128 T = (long long)acc.T, V = (long long)acc.V;
   if (T < 0 || T >= ((__int128)1 << 31) || V < 0 || V >= ((__int128)1 << 62) ||

@@ -9,6 +9,15 @@
 // run concurrently, so requests arriving while others are on the GPU are
 // admitted as soon as a slot and memory free up, and their work overlaps on
 // the device.  Each job's result is what lc_cluster returns for it alone.
+//
+// A job's footprint is its packed input plus the clustering's scratch as
+// estimated by lc::cluster_footprint (the driver's own allocation sizes).
+// An admission's clustering runs with its reserved scratch as the call's
+// scratch limit, so admitted work never holds more than the budget.  A run
+// whose levels shrink too slowly for the estimate stops with LC_ERR_OOM;
+// its jobs then go back to the head of the queue with twice the estimate
+// and wait for memory (a job larger than the whole budget runs alone, with
+// no limit), so callers only see LC_ERR_OOM when the device itself is out.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -21,6 +30,7 @@
 #include <vector>
 
 #include "../../include/lc.h"
+#include "lc_memory.cuh"
 
 namespace {
 
@@ -32,7 +42,8 @@ struct Job {
   std::vector<int64_t> rp, vw;
   std::vector<int32_t> col, ew;
   int64_t mu = 0, Lam = 1;
-  int64_t footprint = 0;
+  int64_t scratch = 0;    // reserved clustering scratch (grows on retry)
+  int64_t footprint = 0;  // input + scratch
   int state = 0;  // 0 queued, 1 running, 2 done
   int rc = LC_OK;
   std::vector<int32_t> labels;
@@ -57,10 +68,10 @@ struct lc_server {
 
 namespace {
 
-// Device bytes a job needs while it runs: its CSR and vertex weights, the
-// per-vertex scratch of the clustering (about 100 bytes per vertex) and the
-// hash-table scratch (16 bytes per stored edge), plus a fixed margin.
-int64_t footprint_of(int64_t n, int64_t nnz) { return 24 * nnz + 120 * n + (1 << 20); }
+// Device bytes of a job's packed input: row pointers, vertex weights,
+// columns, edge weights and labels (cluster_packed's arena), plus room for
+// the provider's rounding of five blocks.
+int64_t input_bytes(int64_t n, int64_t nnz) { return 8 * (n + 1) + 8 * n + 8 * nnz + 4 * n + 5 * 512; }
 
 template <typename T>
 __global__ void k_add_offset(T *__restrict__ a, int64_t count, T add) {
@@ -80,7 +91,8 @@ void add_offset(T *a, int64_t count, T add, cudaStream_t st) {
 // Packs jobs into one CSR on the device (each job copied to its offset,
 // then shifted to global ids) and clusters them in one batched call.
 // labels (host, the packed vertex range) and res[k] are filled on success.
-int cluster_packed(lc_server *s, cudaStream_t st, Job *const *jobs, int count,
+// scratch_limit: the clustering's scratch limit (0: none).
+int cluster_packed(lc_server *s, cudaStream_t st, Job *const *jobs, int count, int64_t scratch_limit,
                    std::vector<int32_t> &labels, std::vector<int64_t> &gptr, lc_result *res) {
   std::vector<int64_t> eptr(count + 1, 0), lam_num(count), lam_den(count);
   gptr.assign(count + 1, 0);
@@ -92,17 +104,14 @@ int cluster_packed(lc_server *s, cudaStream_t st, Job *const *jobs, int count,
   }
   const int64_t n = gptr[count], nnz = eptr[count];
   labels.assign(n > 0 ? n : 1, 0);
-  int rc = LC_OK;
   int64_t *d_rp = nullptr, *d_vw = nullptr;
   int32_t *d_col = nullptr, *d_ew = nullptr, *d_lab = nullptr;
-  if (cudaMallocAsync(&d_rp, 8 * (n + 1), st) != cudaSuccess ||
-      cudaMallocAsync(&d_vw, 8 * (n > 0 ? n : 1), st) != cudaSuccess ||
-      cudaMallocAsync(&d_col, 4 * (nnz > 0 ? nnz : 1), st) != cudaSuccess ||
-      cudaMallocAsync(&d_ew, 4 * (nnz > 0 ? nnz : 1), st) != cudaSuccess ||
-      cudaMallocAsync(&d_lab, 4 * (n > 0 ? n : 1), st) != cudaSuccess) {
-    cudaGetLastError();
-    rc = LC_ERR_OOM;
-  }
+  lc::Arena ar(st, s->cfg.opts);
+  int rc = ar.get(&d_rp, n + 1);
+  if (rc == LC_OK) rc = ar.get(&d_vw, n);
+  if (rc == LC_OK) rc = ar.get(&d_col, nnz);
+  if (rc == LC_OK) rc = ar.get(&d_ew, nnz);
+  if (rc == LC_OK) rc = ar.get(&d_lab, n);
   if (rc == LC_OK) {
     for (int k = 0; k < count; ++k) {
       const Job &j = *jobs[k];
@@ -122,6 +131,7 @@ int cluster_packed(lc_server *s, cudaStream_t st, Job *const *jobs, int count,
     o.stream = st;
     o.event_cb = nullptr;
     o.profile = 0;
+    o.scratch_limit = scratch_limit;
     lc_csr g{n, nnz, d_rp, d_col};
     if (cudaGetLastError() != cudaSuccess) rc = LC_ERR_CUDA;
     if (rc == LC_OK)
@@ -133,33 +143,46 @@ int cluster_packed(lc_server *s, cudaStream_t st, Job *const *jobs, int count,
     }
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
   }
-  if (d_rp) cudaFreeAsync(d_rp, st);
-  if (d_vw) cudaFreeAsync(d_vw, st);
-  if (d_col) cudaFreeAsync(d_col, st);
-  if (d_ew) cudaFreeAsync(d_ew, st);
-  if (d_lab) cudaFreeAsync(d_lab, st);
-  cudaStreamSynchronize(st);
-  return rc;
+  return rc;  // the arena returns the input buffers in stream order
 }
 
 // Clusters an admission.  If the batched call fails (one request breaks a
 // precondition or a guard), every job is run alone so that only the
 // offending ones report an error.
-void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch) {
+// limited: the admission fits the budget, so its scratch is limited to
+// what it reserved.
+void run_batch(lc_server *s, cudaStream_t st, std::vector<Job *> &batch, bool limited) {
   const int count = (int)batch.size();
   std::vector<int32_t> labels;
   std::vector<int64_t> gptr;
   std::vector<lc_result> res(count);
   std::vector<int> rcs(count, LC_OK);
   std::vector<std::vector<int32_t>> own(count);
-  const int rc = cluster_packed(s, st, batch.data(), count, labels, gptr, res.data());
+  int64_t reserved = 0;
+  for (Job *j : batch) reserved += j->scratch;
+  const int rc = cluster_packed(s, st, batch.data(), count, limited ? reserved : 0, labels, gptr, res.data());
+  if (rc == LC_ERR_OOM && limited) {
+    // the estimate was short: back to the head of the queue, in order, with
+    // twice the reservation, to wait for memory
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (int k = count - 1; k >= 0; --k) {
+      Job &j = *batch[k];
+      s->claimed -= j.footprint;
+      j.scratch *= 2;
+      j.footprint = input_bytes(j.n, j.nnz) + j.scratch;
+      j.state = 0;
+      s->queue.push_front(j.id);
+    }
+    s->cv_work.notify_all();
+    return;
+  }
   if (rc == LC_OK) {
     for (int k = 0; k < count; ++k) own[k].assign(labels.begin() + gptr[k], labels.begin() + gptr[k + 1]);
   } else if (count == 1) {
     rcs[0] = rc;
   } else {
     for (int k = 0; k < count; ++k) {
-      rcs[k] = cluster_packed(s, st, &batch[k], 1, labels, gptr, &res[k]);
+      rcs[k] = cluster_packed(s, st, &batch[k], 1, limited ? batch[k]->scratch : 0, labels, gptr, &res[k]);
       if (rcs[k] == LC_OK) own[k].assign(labels.begin(), labels.begin() + batch[k]->n);
     }
   }
@@ -189,6 +212,7 @@ void worker(lc_server *s) {
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (;;) {
     std::vector<Job *> batch;
+    bool limited = true;
     {
       std::unique_lock<std::mutex> lock(s->mu);
       for (;;) {
@@ -205,7 +229,10 @@ void worker(lc_server *s) {
             if (!fits && !alone) break;
             batch.push_back(&j);
             add += j.footprint;
-            if (!fits) break;
+            if (!fits) {
+              limited = false;
+              break;
+            }
           }
           if (!batch.empty()) {
             for (size_t k = 0; k < batch.size(); ++k) {
@@ -220,7 +247,7 @@ void worker(lc_server *s) {
       }
     }
     if (batch.empty()) break;
-    run_batch(s, st, batch);
+    run_batch(s, st, batch, limited);
   }
   cudaStreamDestroy(st);
 }
@@ -254,6 +281,7 @@ LC_API int lc_server_create(const lc_server_config *cfg, lc_server **out) {
   lc_server_default_config(&c);
   if (cfg) c = *cfg;
   if (c.slots < 1 || c.slots > 64 || c.max_batch < 1 || c.hbm_budget < 0) return LC_ERR_ARG;
+  if ((c.opts.alloc == nullptr) != (c.opts.dealloc == nullptr)) return LC_ERR_ARG;
   lc_server *s = new lc_server();
   s->cfg = c;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -297,7 +325,8 @@ LC_API int lc_server_submit(lc_server *s, const lc_csr *g, const int64_t *vertex
   }
   j.mu = lambda_num;
   j.Lam = lambda_den;
-  j.footprint = footprint_of(g->n, g->nnz);
+  j.scratch = lc::cluster_footprint(g->n, g->nnz, 1, s->cfg.opts);
+  j.footprint = input_bytes(g->n, g->nnz) + j.scratch;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) return LC_ERR_ARG;

@@ -57,10 +57,12 @@ def test_struct_layouts_match_c(tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "lc.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\\n\", sizeof(lc_opts),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\\n\","
+        " sizeof(lc_opts),"
         " sizeof(lc_result), sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream),"
         " offsetof(lc_result, error_detail), sizeof(lc_server_config), offsetof(lc_server_config, opts),"
         " offsetof(lc_opts, tables), offsetof(lc_result, kernel_bytes), offsetof(lc_result, tables_rebuilt),"
+        " offsetof(lc_opts, alloc), offsetof(lc_opts, alloc_ctx), offsetof(lc_result, scratch_peak_bytes),"
         " (int)LC_K_COUNT);"
         "return 0;}\n")
     exe = tmp_path / "sizes"
@@ -69,7 +71,9 @@ def test_struct_layouts_match_c(tmp_path):
     assert vals == [ctypes.sizeof(lc._Opts), ctypes.sizeof(lc._Result), ctypes.sizeof(lc._Event),
                     ctypes.sizeof(lc._Csr), lc._Opts.stream.offset, lc._Result.error_detail.offset,
                     ctypes.sizeof(lc._ServerConfig), lc._ServerConfig.opts.offset, lc._Opts.tables.offset,
-                    lc._Result.kernel_bytes.offset, lc._Result.tables_rebuilt.offset, len(lc.LC_K_NAMES)]
+                    lc._Result.kernel_bytes.offset, lc._Result.tables_rebuilt.offset,
+                    lc._Opts.alloc.offset, lc._Opts.alloc_ctx.offset, lc._Result.scratch_peak_bytes.offset,
+                    len(lc.LC_K_NAMES)]
 
 
 def test_defaults_and_strerror(lib):
@@ -82,6 +86,9 @@ def test_defaults_and_strerror(lib):
     assert o.uncoarsen == 1 and o.validate == 1
     assert lc.lc_strerror(0) == "ok"
     assert "symmetric" in lc.lc_strerror(2)
+    assert not o.alloc and not o.dealloc and not o.alloc_ctx  # the library's own pool
+    assert lc._c_opts(lc.Options(), None).alloc  # the binding passes PyTorch's allocator
+    assert not lc._c_opts(lc.Options(allocator="library"), None).alloc
     cfg = lc.lc_server_default_config()
     assert cfg.slots == 4 and cfg.max_batch == 64 and cfg.hbm_budget == 0
     assert cfg.opts.pass_limit == 6
@@ -96,3 +103,19 @@ def test_product_path_does_not_reference_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lc_oracle" not in text and "liboracle" not in text, f
+
+
+def test_scratch_estimate_matches_the_driver_sizes(lib):
+    """lc_scratch_estimate grows with the graph, counts the kept-table
+    buffers and rejects bad sizes (no GPU needed: host arithmetic)."""
+    import paper_2608_01503_gb300 as lc
+
+    a = lc.lc_scratch_estimate(1000, 10000)
+    b = lc.lc_scratch_estimate(2000, 20000)
+    assert 0 < a < b
+    # at least the level-0 hash table (16 B per stored edge) and 11 int32 arrays per vertex
+    assert a >= 16 * 10000 + 44 * 1000
+    assert lc.lc_scratch_estimate(1000, 10000, opts=lc.Options(tables=1)) > a
+    assert lc.lc_scratch_estimate(1000, 10000, count=8) > a
+    assert lib.lc_scratch_estimate(-1, 0, 1, None) == -1
+    assert lib.lc_scratch_estimate(10, 0, 0, None) == -1

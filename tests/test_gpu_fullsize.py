@@ -1,8 +1,9 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (profiling on, the default schedule).  The oracle runs each whole
 clustering on the host (about a minute per graph for R-MAT scale 22 and the
-256^3 grid); the batched and served workloads are checked on a sample of
-their graphs, each clustered alone by the oracle."""
+256^3 grid); every graph of the batched workload and of the served
+workload's request pool is clustered alone by the oracle, the graphs spread
+over the host's cores."""
 import numpy as np
 import pytest
 
@@ -42,7 +43,7 @@ def test_grid256_whole_run():
     check_whole(gg.grid_cpm(side=256))
 
 
-def test_batched_4096_sampled():
+def test_batched_4096_every_graph():
     graphs = gg.batched_sbms(4096, seed=3)
     b = gg.pack(graphs)
     labels, res = lc.lc_cluster_batch(dev(b["row_ptr"]), dev(b["col"]), dev(b["ew"]), dev(b["vw"]),
@@ -51,31 +52,25 @@ def test_batched_4096_sampled():
     torch.cuda.synchronize()
     labels = labels.cpu().numpy()
     gp = b["graph_ptr"]
-    # every 97th graph plus the largest one
-    sample = sorted(set(range(0, 4096, 97)) | {int(np.argmax([g.nnz for g in graphs]))})
-    for k in sample:
-        ref, ores, _ = oracle.louvain_plus(graphs[k])
+    refs = oracle.louvain_plus_many(graphs)
+    for k, (ref, ores) in enumerate(refs):
         assert np.array_equal(labels[gp[k]:gp[k + 1]], ref), k
-        assert res[k]["phi"] == ores["phi"] and res[k]["n_clusters"] == ores["n_clusters"], k
+        for key in ("phi", "n_clusters", "levels", "modularity"):
+            assert res[k][key] == ores[key], (k, key)
 
 
-def test_served_mix_sampled():
-    """The served workload's largest SBM and R-MAT requests and a few small
-    ones, submitted together so they share admissions."""
-    params = gg.served_request_params(64, seed=4)
+def test_served_pool_every_request():
+    """The served workload's whole 64-graph request pool, submitted together
+    so that requests share admissions and slots overlap on the device."""
     graphs = gg.served_requests(64, seed=4)
-    sbm = [k for k, p in enumerate(params) if p[0] == "sbm"]
-    rmat = [k for k, p in enumerate(params) if p[0] == "rmat"]
-    big = [max(sbm, key=lambda k: graphs[k].n), max(rmat, key=lambda k: graphs[k].n)]
-    pick = big + sbm[:3] + rmat[:3]
-    with lc.Server(slots=2, max_batch=8) as srv:
-        ids = [srv.submit(graphs[k].row_ptr, graphs[k].col, graphs[k].ew, graphs[k].vw,
-                          graphs[k].lam_num, graphs[k].lam_den) for k in pick]
+    with lc.Server(slots=4, max_batch=8) as srv:
+        ids = [srv.submit(g.row_ptr, g.col, g.ew, g.vw, g.lam_num, g.lam_den) for g in graphs]
         out = [srv.wait(j) for j in ids]
-    for k, (labels, res, _) in zip(pick, out):
-        ref, ores, _ = oracle.louvain_plus(graphs[k])
-        assert np.array_equal(labels, ref), graphs[k].name
-        assert res["phi"] == ores["phi"], graphs[k].name
+    refs = oracle.louvain_plus_many(graphs)
+    for g, (labels, res, _), (ref, ores) in zip(graphs, out, refs):
+        assert np.array_equal(labels, ref), g.name
+        for key in ("phi", "n_clusters", "levels", "modularity"):
+            assert res[key] == ores[key], (g.name, key)
 
 
 def test_rmat22_pleiden_whole_run():

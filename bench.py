@@ -55,9 +55,10 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes per step of a kernel class, from one ncu capture of the same
-# kernels on the same workload (profiles/dram_rmat22.md); null elsewhere.
-TRAFFIC_PER_STEP = {("rmat22", "move"): 46.155e9}
+# DRAM bytes per step of a kernel class, from one ncu capture (dram__bytes_read
+# + dram__bytes_write over every launch of the class) of the same kernels on
+# the same workload; a class whose kernels changed since has none (null).
+TRAFFIC_PER_STEP = {}
 
 
 def make_graph(name: str, scale_override: int | None = None):
@@ -135,73 +136,110 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(workload: str, budget_s: float = 20.0, method: str = "louvain+"):
-    """The CPU oracle (single thread, as it stands) on a bounded sample of the
-    workload family, reported in the metric's unit."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def _oracle_run(g, method):
+    import oracle
+
+    if method == "louvain+":
+        return oracle.louvain_plus(g)
+    return oracle.pleiden(g, oracle.Params(uncoarsen=method == "leiden+"))
+
+
+def cpu_baseline(workload: str, g_full=None, method: str = "louvain+"):
+    """The CPU oracle as it stands, timed on this host: its OpenMP build
+    (the same source, every pass and contraction loop on all cores) once on
+    the benchmarked graph itself, and the sequential build on a bounded
+    sample of the same recipe.  Both in the metric's unit."""
     import graphgen as gg
     import oracle
 
-    if workload == "rmat22":
-        scale = 18
-        g = gg.rmat(scale, 16, seed=1, wmax=8)
-        sample = f"full Louvain+ on R-MAT scale {scale} (same generator, edge factor, weights, objective)"
-    elif workload == "grid256":
-        g = gg.grid_cpm(side=64)
-        sample = "full Louvain+ on the 64^3 grid of the same recipe (CPM 1/100)"
-    else:
-        g = gg.sbm_planted()
-        sample = "full Louvain+ on the same SBM graph"
-    if method != "louvain+":
-        sample = sample.replace("Louvain+", {"leiden": "pLeiden", "leiden+": "pLeiden+"}[method])
-    runs, t_total = 0, 0.0
-    while t_total < budget_s and runs < 5:
+    name = {"louvain+": "Louvain+", "leiden": "pLeiden", "leiden+": "pLeiden+"}[method]
+    cores = host_cores()
+    g = g_full if g_full is not None else make_graph(workload)
+    with oracle.all_cores():
         t0 = time.perf_counter()
-        if method == "louvain+":
-            oracle.louvain_plus(g)
-        else:
-            oracle.pleiden(g, oracle.Params(uncoarsen=method == "leiden+"))
-        t_total += time.perf_counter() - t0
-        runs += 1
-    return {"value": g.nnz * runs / t_total, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": sample + f"; {runs} run(s), {t_total:.1f} s; nnz={g.nnz}"}
+        _oracle_run(g, method)
+        t_all = time.perf_counter() - t0
+    if workload == "rmat22":
+        g1, s1 = gg.rmat(20, 16, seed=1, wmax=8), "R-MAT scale 20 of the same recipe"
+    elif workload == "grid256":
+        g1, s1 = gg.grid_cpm(side=128), "the 128^3 grid of the same recipe (CPM 1/100)"
+    else:
+        g1, s1 = g, "the same graph"
+    t0 = time.perf_counter()
+    _oracle_run(g1, method)
+    t_one = time.perf_counter() - t0
+    return {"value": g.nnz / t_all, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "sample": f"full {name} on the benchmarked graph itself (nnz={g.nnz}), OpenMP build of "
+                      f"the oracle on all {cores} host cores, one run, {t_all:.1f} s",
+            "cpu_model": cpu_model(),
+            "one_thread": {"value": g1.nnz / t_one, "unit": "edges/s", "cores": 1,
+                           "sample": f"full {name} on {s1} (nnz={g1.nnz}), sequential build, "
+                                     f"one run, {t_one:.1f} s"}}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle timed as it stands on the host cores,
-    one bounded sample of the workload per step, in the metric's unit."""
+    """--impl reference: the CPU oracle timed as it stands on the host's
+    cores, one bounded sample of the workload per step, in the metric's
+    unit.  Single graphs use the oracle's OpenMP build (every pass and
+    contraction loop on all cores); the batched and served samples spread
+    their graphs over the cores instead (one sequential oracle call each)."""
     if rank != 0:
         return
     import graphgen as gg
     import oracle
 
     unit = "edges/s"
+    cores = host_cores()
     if args.workload == "batched":
-        graphs = gg.batched_sbms(args.count, seed=3, indices=list(range(0, args.count, 64)))
-        sample = f"every 64th graph of the batched workload ({len(graphs)} graphs), one oracle call each"
+        graphs = gg.batched_sbms(args.count, seed=3, indices=list(range(0, args.count, 16)))
+        sample = f"every 16th graph of the batched workload ({len(graphs)} graphs) on {cores} host threads"
         unit = "graphs/s"
     elif args.workload == "served":
         graphs = gg.served_requests(8, seed=4)
-        sample = "the first 8 requests of the served stream, one oracle call each"
+        sample = f"the first 8 requests of the served stream on {cores} host threads"
         unit = "graphs/s"
     elif args.workload == "rmat22":
-        graphs = [gg.rmat(17, 16, seed=1, wmax=8)]
-        sample = "R-MAT scale 17 sample of the workload (same recipe)"
+        graphs = [gg.rmat(21, 16, seed=1, wmax=8)]
+        sample = f"R-MAT scale 21 of the same recipe, OpenMP oracle on {cores} host cores"
     elif args.workload == "grid256":
-        graphs = [gg.grid_cpm(side=48)]
-        sample = "48^3 grid sample of the workload (same recipe)"
+        graphs = [gg.grid_cpm(side=200)]
+        sample = f"the 200^3 grid of the same recipe, OpenMP oracle on {cores} host cores"
     else:
         graphs = [gg.sbm_planted()]
-        sample = "the SBM graph itself"
+        sample = f"the SBM graph itself, OpenMP oracle on {cores} host cores"
     method = getattr(args, "method", "louvain+")
     if method != "louvain+":
         sample += f"; {'pLeiden+' if method == 'leiden+' else 'pLeiden'}"
+    many = unit == "graphs/s"
 
     def one_step():
-        for g in graphs:
-            if method == "louvain+":
-                oracle.louvain_plus(g)
-            else:
-                oracle.pleiden(g, oracle.Params(uncoarsen=method == "leiden+"))
+        if many:
+            oracle.louvain_plus_many(graphs)
+        else:
+            with oracle.all_cores():
+                for g in graphs:
+                    _oracle_run(g, method)
 
     for _ in range(args.warmup):
         one_step()
@@ -209,7 +247,7 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         one_step()
     dt = time.perf_counter() - t0
-    per_step = len(graphs) if unit == "graphs/s" else sum(g.nnz for g in graphs)
+    per_step = len(graphs) if many else sum(g.nnz for g in graphs)
     value = per_step * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
@@ -217,7 +255,8 @@ def run_reference(args, rank, world):
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
                        "sample": sample, "nnz": sum(g.nnz for g in graphs)},
-            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -710,7 +749,7 @@ def main():
         "gpu_launches": int(sum(klaunch.values())),
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, method=args.method)
+        line["cpu_baseline"] = cpu_baseline(args.workload, g, method=args.method)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -29,20 +29,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lc_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIBDIR, "liboracle_omp.so")
 
-GCC_FLAGS = ["-O2", "-std=gnu11", "-shared", "-fPIC", "-Wall", "-Wextra"]
+GCC_FLAGS = ["-O2", "-std=gnu11", "-shared", "-fPIC", "-Wall", "-Wextra", "-Wno-unknown-pragmas"]
 
 NONE = -1
 EMPTY = -2
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compiles lc_oracle.c: sequentially, or with -fopenmp (the same source,
+    its pass and contraction loops spread over the host's cores with
+    identical results; the all-core CPU baseline)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp"
-        subprocess.check_call(["gcc", *GCC_FLAGS, _SRC, "-o", tmp])
-        os.replace(tmp, _LIB)
-    return _LIB
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", *GCC_FLAGS, *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp])
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Graph(ctypes.Structure):
@@ -130,6 +135,15 @@ def _load():
         if _lib is None:
             _lib = _bind(ctypes.CDLL(build()))
         return _lib
+
+
+@contextlib.contextmanager
+def all_cores():
+    """Runs the oracle's OpenMP build while the context is open: the same
+    passes and contractions, each loop over vertices or clusters spread over
+    the host's cores (OMP_NUM_THREADS, else all of them)."""
+    with library(build(openmp=True)):
+        yield
 
 
 @contextlib.contextmanager

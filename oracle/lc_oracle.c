@@ -51,8 +51,25 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef __int128 i128;
+
+/* Built with -fopenmp (the all-core CPU baseline), the loops over vertices
+ * inside one synchronous pass and over clusters inside one contraction run
+ * on all threads.  Every iteration writes only its own vertex's or
+ * cluster's entries, each thread has its own accumulation scratch, and the
+ * reductions are integer sums, so the results are identical to the
+ * sequential build (which ignores the pragmas). */
+#ifdef _OPENMP
+static int orc_threads(void) { return omp_get_max_threads(); }
+static int orc_thread(void) { return omp_get_thread_num(); }
+#else
+static int orc_threads(void) { return 1; }
+static int orc_thread(void) { return 0; }
+#endif
 
 /* ------------------------------------------------------------ types --- */
 
@@ -138,7 +155,8 @@ static void cluster_weights(const orc_graph *g, const int32_t *C, int64_t *W) {
  *              - lambda * sum_i sum_{u != v in C_i} w(u) w(v)
  * with sum_{u != v in C_i} w(u) w(v) = W(C_i)^2 - sum_{v in C_i} w(v)^2. */
 static i128 objective(const orc_graph *g, int64_t mu, int64_t Lam, const int32_t *C, int64_t *Wscratch) {
-  i128 env = 0;
+  int64_t env = 0; /* at most the sum of all stored weights: nnz < 2^32 entries below 2^31 */
+#pragma omp parallel for schedule(static) reduction(+ : env)
   for (int64_t v = 0; v < g->n; v++)
     for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++)
       if (C[g->col[e]] == C[v]) env += g->ew[e];
@@ -212,7 +230,7 @@ static int earlier(int64_t u, int64_t v, const int64_t *q, uint32_t seed) {
 
 typedef struct {
   int64_t n;
-  int64_t *W, *acc, *delta, *q, *adj, *gC;
+  int64_t *W, *acc, *delta, *q, *adj, *gC; /* acc and touched: one n-slice per thread */
   int32_t *touched, *D, *C_before, *C_next, *mark, *Bc;
   uint8_t *in_L, *in_M;
 } work;
@@ -240,12 +258,13 @@ static int work_alloc(work *w, int64_t n) {
   size_t m = (size_t)(n > 0 ? n : 1);
   w->n = n;
   w->W = calloc(m, 8);
-  w->acc = calloc(m, 8);
+  const size_t mt = m * (size_t)orc_threads();
+  w->acc = calloc(mt, 8);
   w->delta = calloc(m, 8);
   w->q = calloc(m, 8);
   w->adj = calloc(m, 8);
   w->gC = calloc(m, 8);
-  w->touched = calloc(m, 4);
+  w->touched = calloc(mt, 4);
   w->D = calloc(m, 4);
   w->C_before = calloc(m, 4);
   w->C_next = calloc(m, 4);
@@ -293,29 +312,32 @@ static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, 
   }
 
   /* Algorithm 2, parallel loop over V: D[v] = argmax over C \ C[v]. */
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : nL)
   for (int64_t v = 0; v < n; v++) {
+    int64_t *acc = w->acc + (int64_t)orc_thread() * n; /* zero between vertices */
+    int32_t *touched = w->touched + (int64_t)orc_thread() * n;
     int64_t nt = 0;
     for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
       int32_t X = C[g->col[e]];
-      if (w->acc[X] == 0) w->touched[nt++] = X;
-      w->acc[X] += g->ew[e];
+      if (acc[X] == 0) touched[nt++] = X;
+      acc[X] += g->ew[e];
     }
     const int32_t Cv = C[v];
     const int64_t wv = g->vw[v];
-    const i128 gC = (i128)Lam * w->acc[Cv] - (i128)mu * wv * (w->W[Cv] - wv);
+    const i128 gC = (i128)Lam * acc[Cv] - (i128)mu * wv * (w->W[Cv] - wv);
     int32_t best = ORC_NONE;
     i128 gbest = 0;
     for (int64_t t = 0; t < nt; t++) {
-      const int32_t X = w->touched[t];
+      const int32_t X = touched[t];
       if (X == Cv) continue;
       if (B && (B[v] == ORC_MIXED || w->Bc[X] != B[v])) continue; /* the constraint forbids X */
-      const i128 gX = (i128)Lam * w->acc[X] - (i128)mu * wv * w->W[X];
+      const i128 gX = (i128)Lam * acc[X] - (i128)mu * wv * w->W[X];
       if (best == ORC_NONE || gX > gbest || (gX == gbest && X < best)) {
         best = X;
         gbest = gX;
       }
     }
-    for (int64_t t = 0; t < nt; t++) w->acc[w->touched[t]] = 0;
+    for (int64_t t = 0; t < nt; t++) acc[touched[t]] = 0;
     /* empty-cluster rule: both w'(v,C[v]) and w'(v,D[v]) negative */
     if (gC < 0 && (best == ORC_NONE || gbest < 0)) {
       best = ORC_EMPTY;
@@ -334,6 +356,7 @@ static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, 
   }
 
   /* ordering keys of the candidates */
+#pragma omp parallel for schedule(static)
   for (int64_t v = 0; v < n; v++)
     if (w->in_L[v])
       w->q[v] = (int64_t)floordiv128((i128)p->eps_den * w->delta[v], (i128)p->eps_num * Lam);
@@ -359,7 +382,9 @@ static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, 
   }
 
   /* Algorithm 3: afterburner filter. */
-  for (int64_t v = 0; v < n && p->symmetry == 0; v++) {
+  const int64_t n_ab = p->symmetry == 0 ? n : 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : nM)
+  for (int64_t v = 0; v < n_ab; v++) {
     if (!w->in_L[v]) continue;
     i128 d = w->delta[v];
     const int32_t Cv = C[v], Dv = w->D[v];
@@ -386,6 +411,7 @@ static void one_pass(const orc_graph *g, const orc_params *p, const int32_t *B, 
    * movers receive the ids that are unused once every move is applied,
    * ascending ids to ascending vertices. */
   memcpy(w->C_next, C, (size_t)n * sizeof(int32_t));
+#pragma omp parallel for schedule(static)
   for (int64_t v = 0; v < n; v++)
     if (w->in_M[v] && w->D[v] >= 0) w->C_next[v] = w->D[v];
   memset(w->mark, 0, (size_t)n * sizeof(int32_t));
@@ -527,21 +553,40 @@ static int cmp_i32(const void *a, const void *b) {
   return (x > y) - (x < y);
 }
 
+/* The distinct coarse neighbours y != x of cluster x with their summed
+ * weights (sorted by y) into touched[0..nt) / acc[touched[t]]; acc must be
+ * zero on entry and is left holding the sums (the caller clears them). */
+static int64_t coarse_row(const orc_graph *g, const int32_t *C, const int64_t *mem_ptr,
+                          const int32_t *members, int64_t x, int64_t *acc, int32_t *touched,
+                          int64_t *vw_x) {
+  int64_t nt = 0, wx = 0;
+  for (int64_t k = mem_ptr[x]; k < mem_ptr[x + 1]; k++) {
+    const int64_t v = members[k];
+    wx += g->vw[v];
+    for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+      const int32_t y = C[g->col[e]];
+      if (y == x) continue;
+      if (acc[y] == 0) touched[nt++] = y;
+      acc[y] += g->ew[e];
+    }
+  }
+  qsort(touched, (size_t)nt, 4, cmp_i32);
+  *vw_x = wx;
+  return nt;
+}
+
 static int contract(const orc_graph *g, const int32_t *C, int64_t n_c, orc_owned_graph *out) {
   memset(out, 0, sizeof(*out));
   const int64_t n = g->n;
-  size_t mc = (size_t)(n_c > 0 ? n_c : 1);
+  const size_t mc = (size_t)(n_c > 0 ? n_c : 1), nthr = (size_t)orc_threads();
   int64_t *mem_ptr = calloc(mc + 1, 8); /* members of each cluster (counting sort) */
   int32_t *members = malloc((size_t)(n > 0 ? n : 1) * 4);
-  int64_t *acc = calloc(mc, 8);
-  int32_t *touched = malloc(mc * 4);
+  int64_t *acc = calloc(mc * nthr, 8);    /* one n_c-slice per thread */
+  int32_t *touched = malloc(mc * nthr * 4);
   out->row_ptr = calloc(mc + 1, 8);
   out->vw = calloc(mc, 8);
-  int64_t cap = 1024, len = 0;
-  out->col = malloc((size_t)cap * 4);
-  out->ew = malloc((size_t)cap * 4);
   int rc = ORC_OK;
-  if (!mem_ptr || !members || !acc || !touched || !out->row_ptr || !out->vw || !out->col || !out->ew) {
+  if (!mem_ptr || !members || !acc || !touched || !out->row_ptr || !out->vw) {
     rc = ORC_ERR_OOM;
     goto done;
   }
@@ -557,41 +602,36 @@ static int contract(const orc_graph *g, const int32_t *C, int64_t n_c, orc_owned
     for (int64_t v = 0; v < n; v++) members[fill[C[v]]++] = (int32_t)v;
     free(fill);
   }
+  /* pass 1: row lengths and coarse vertex weights */
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t x = 0; x < n_c; x++) {
-    int64_t nt = 0;
-    for (int64_t k = mem_ptr[x]; k < mem_ptr[x + 1]; k++) {
-      const int64_t v = members[k];
-      out->vw[x] += g->vw[v];
-      for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
-        const int32_t y = C[g->col[e]];
-        if (y == x) continue;
-        if (acc[y] == 0) touched[nt++] = y;
-        acc[y] += g->ew[e];
-      }
+    int64_t *a = acc + (int64_t)orc_thread() * (int64_t)mc;
+    int32_t *t = touched + (int64_t)orc_thread() * (int64_t)mc;
+    const int64_t nt = coarse_row(g, C, mem_ptr, members, x, a, t, &out->vw[x]);
+    for (int64_t k = 0; k < nt; k++) a[t[k]] = 0;
+    out->row_ptr[x + 1] = nt;
+  }
+  for (int64_t x = 0; x < n_c; x++) out->row_ptr[x + 1] += out->row_ptr[x];
+  const int64_t len = out->row_ptr[n_c > 0 ? n_c : 0];
+  out->col = malloc((size_t)(len > 0 ? len : 1) * 4);
+  out->ew = malloc((size_t)(len > 0 ? len : 1) * 4);
+  if (!out->col || !out->ew) {
+    rc = ORC_ERR_OOM;
+    goto done;
+  }
+  /* pass 2: the rows, sorted by column */
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t x = 0; x < n_c; x++) {
+    int64_t *a = acc + (int64_t)orc_thread() * (int64_t)mc;
+    int32_t *t = touched + (int64_t)orc_thread() * (int64_t)mc;
+    int64_t wx;
+    const int64_t nt = coarse_row(g, C, mem_ptr, members, x, a, t, &wx);
+    const int64_t o = out->row_ptr[x];
+    for (int64_t k = 0; k < nt; k++) {
+      out->col[o + k] = t[k];
+      out->ew[o + k] = (int32_t)a[t[k]];
+      a[t[k]] = 0;
     }
-    qsort(touched, (size_t)nt, 4, cmp_i32);
-    if (len + nt > cap) {
-      while (len + nt > cap) cap *= 2;
-      int32_t *nc = realloc(out->col, (size_t)cap * 4), *nw;
-      if (!nc) {
-        rc = ORC_ERR_OOM;
-        goto done;
-      }
-      out->col = nc;
-      nw = realloc(out->ew, (size_t)cap * 4);
-      if (!nw) {
-        rc = ORC_ERR_OOM;
-        goto done;
-      }
-      out->ew = nw;
-    }
-    for (int64_t t = 0; t < nt; t++) {
-      out->col[len] = touched[t];
-      out->ew[len] = (int32_t)acc[touched[t]];
-      len++;
-      acc[touched[t]] = 0;
-    }
-    out->row_ptr[x + 1] = len;
   }
   out->n = n_c;
   out->nnz = len;

@@ -283,9 +283,18 @@ def _max_over_ranks(dist, x, dev):
     return float(t.item())
 
 
+def _gpu_key(workload: str) -> str:
+    import torch
+
+    return f"{workload}/{torch.cuda.get_device_name()}"
+
+
 def run_batched(args, rank, world):
     """Batched form: all graphs in one lc_cluster_batch call per step;
     the plain path clusters a stratified sample one lc_cluster call at a time.
+    Timed three ways: the hand-picked default launch settings, the settings
+    lc_autotune chose for this workload (tuning.json, or a fresh tune with
+    --tune), and the tuned bins with CUDA-graph replay switched the other way.
     With N ranks each clusters its share of the graphs (longest-processing-
     time by expected stored edges); no collective touches the data."""
     import torch
@@ -306,32 +315,50 @@ def run_batched(args, rank, world):
     rp, col, ew, vw = t(b["row_ptr"]), t(b["col"]), t(b["ew"]), t(b["vw"])
     labels = torch.empty(rp.numel() - 1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts = lc.Options(profile=True)
+    call = lambda o: lc.lc_cluster_batch(rp, col, ew, vw, b["graph_ptr"], b["lam_num"], b["lam_den"], opts=o,
+                                         labels_out=labels)
+    key = _gpu_key("batched" if count == 4096 else f"batched{count}")
+    tuning = None if args.no_tuning else lc.load_tuning(key)
+    if args.tune:
+        tuning = lc.lc_autotune(rp, col, ew, vw, b["lam_num"], b["lam_den"], graph_ptr=b["graph_ptr"], repeats=2)
+        if rank == 0:
+            lc.save_tuning(key, tuning)
+    arms = {"default": lc.Options()}
+    if tuning:
+        arms["tuned"] = lc.tuned_options(tuning)
+        arms["tuned_graphs_" + ("off" if tuning["graphs"] else "on")] = lc.tuned_options(
+            tuning, graphs=not tuning["graphs"])
+    else:
+        arms["default_graphs_on"] = lc.Options(graphs=True)
+    main = "tuned" if tuning else "default"
+    # per-class breakdown from one profiled run of the main setting (not timed)
+    opts_prof = lc.tuned_options(tuning, profile=True) if tuning else lc.Options(profile=True)
     for _ in range(args.warmup):
-        lc.lc_cluster_batch(rp, col, ew, vw, b["graph_ptr"], b["lam_num"], b["lam_den"], opts=opts,
-                            labels_out=labels)
+        for o in arms.values():
+            call(o)
+    _, pres = call(opts_prof)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    klaunch, kms = 0, {}
-    ev0.record(stream)
-    for _ in range(args.steps):
-        _, res = lc.lc_cluster_batch(rp, col, ew, vw, b["graph_ptr"], b["lam_num"], b["lam_den"],
-                                     opts=opts, labels_out=labels)
-        klaunch += sum(res[0]["kernel_launches"].values())
-        for k, v in res[0]["kernel_ms"].items():
-            kms[k] = kms.get(k, 0.0) + v
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
+    arm_ms, klaunch = {}, 0
+    for name, o in arms.items():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, res = call(o)
+            if name == main:
+                klaunch += sum(res[0]["kernel_launches"].values())
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        arm_ms[name] = _max_over_ranks(dist, ev0.elapsed_time(ev1) / args.steps, dev)
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms_step = _max_over_ranks(dist, ev0.elapsed_time(ev1) / args.steps, dev)
+    ms_step = arm_ms[main]
     # plain: one lc_cluster call per graph, every 16th graph (device-resident)
     sample = graphs[::16]
     dg = [(t(g.row_ptr), t(g.col), t(g.ew), t(g.vw), g.lam_num, g.lam_den) for g in sample]
@@ -346,6 +373,8 @@ def run_batched(args, rank, world):
     torch.cuda.synchronize(dev)
     plain_s = time.perf_counter() - p0
     # identical results in both forms
+    call(arms[main])
+    torch.cuda.synchronize(dev)
     gp = b["graph_ptr"]
     same = all(torch.equal(labels[gp[16 * i]:gp[16 * i + 1]], plain_labels[i]) for i in range(len(sample)))
     nnz = int(b["col"].shape[0])
@@ -360,12 +389,15 @@ def run_batched(args, rank, world):
             "config": {"workload": "batched", "description": WORKLOADS["batched"]["desc"], "graphs": count,
                        "n_rank0": int(rp.numel() - 1), "nnz": nnz,
                        "sharding": "graphs split over ranks by expected edges (LPT); no data collective",
-                       "l2": "inputs larger than L2; no flush"},
+                       "l2": "inputs larger than L2; no flush", "settings": main,
+                       "tuning": tuning},
             "edges_per_s": nnz / (ms_step / 1000.0),
+            "arms_ms_per_step": arm_ms,
+            "arms_graphs_per_s": {k: count / (v / 1000.0) for k, v in arm_ms.items()},
             "plain": {"graphs_per_s": len(sample) / plain_s, "sample": f"every 16th graph ({len(sample)})",
                       "identical_labels": bool(same)},
             "speedup_vs_plain": value / (len(sample) / plain_s),
-            "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "breakdown_ms_per_step": pres[0]["kernel_ms"],
             "clocks": clocks, "gpu_launches": int(klaunch)}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -378,10 +410,11 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
 
 
-def _served_arm(lc, reqs, arrivals, slots, max_batch):
+def _served_arm(lc, reqs, arrivals, slots, max_batch, graphs=False):
     """Submits reqs[i] at arrivals[i] seconds; returns (latencies, makespan, launches)."""
     lat, done, launches = [], [], 0
-    with lc.Server(slots=slots, max_batch=max_batch) as srv:
+    opts = lc.Options(allocator="library", graphs=graphs)
+    with lc.Server(slots=slots, max_batch=max_batch, opts=opts) as srv:
         ids, t_call = [], []
         t0 = time.perf_counter()
         for g, ta in zip(reqs, arrivals):
@@ -461,10 +494,15 @@ def run_served(args, rank, world):
     time.sleep(0.3)
     if dist:
         dist.barrier()
-    lat, span, launches = _served_arm(lc, reqs, [0.0] * len(reqs), args.slots, args.max_batch)
-    span = _max_over_ranks(dist, span, dev)
-    lat = all_lat(lat)
+    sat = {}
+    for gmode in (False, True):  # CUDA-graph replay of repeated passes off / on
+        if dist:
+            dist.barrier()
+        lat_g, span_g, launches_g = _served_arm(lc, reqs, [0.0] * len(reqs), args.slots, args.max_batch, gmode)
+        sat[gmode] = (all_lat(lat_g), _max_over_ranks(dist, span_g, dev), launches_g)
     clocks = sampler.stop()
+    graphs_main = sat[True][1] < sat[False][1]
+    lat, span, launches = sat[graphs_main]
     value = R / span
     rates = []
     for k, f in enumerate(float(x) for x in args.rates.split(",") if x):
@@ -474,21 +512,22 @@ def run_served(args, rank, world):
         arr = [float(a - arr[0]) for a in arr][rank::world]
         t0 = arr[0] if arr else 0.0
         arr = [a - t0 for a in arr]
-        if dist:
-            dist.barrier()
-        s_lat, s_span, _ = _served_arm(lc, reqs, arr, args.slots, args.max_batch)
-        s_span = _max_over_ranks(dist, s_span, dev)
-        s_lat = all_lat(s_lat)
+        row = {"rate_vs_plain": f, "offered_per_s": rate}
+        for gmode in (graphs_main, not graphs_main):
+            if dist:
+                dist.barrier()
+            s_lat, s_span, _ = _served_arm(lc, reqs, arr, args.slots, args.max_batch, gmode)
+            s_span = _max_over_ranks(dist, s_span, dev)
+            s_lat = all_lat(s_lat)
+            row["served" if gmode == graphs_main else "served_graphs_" + ("on" if gmode else "off")] = {
+                "p50_s": _pct(s_lat, 0.5), "p99_s": _pct(s_lat, 0.99), "graphs_per_s": R / s_span}
         if dist:
             dist.barrier()
         p_lat, p_span, _ = _plain_arm(lc, reqs, arr)
         p_span = _max_over_ranks(dist, p_span, dev)
         p_lat = all_lat(p_lat)
-        rates.append({"rate_vs_plain": f, "offered_per_s": rate,
-                      "served": {"p50_s": _pct(s_lat, 0.5), "p99_s": _pct(s_lat, 0.99),
-                                 "graphs_per_s": R / s_span},
-                      "plain": {"p50_s": _pct(p_lat, 0.5), "p99_s": _pct(p_lat, 0.99),
-                                "graphs_per_s": R / p_span}})
+        row["plain"] = {"p50_s": _pct(p_lat, 0.5), "p99_s": _pct(p_lat, 0.99), "graphs_per_s": R / p_span}
+        rates.append(row)
     line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": R,
             "warmup": args.warmup, "ms_per_step": span * 1000.0 / R, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -498,7 +537,11 @@ def run_served(args, rank, world):
                        "sharding": "request i served by rank i mod N; no data collective",
                        "l2": "each request's arrays are new to the device; no flush"},
             "saturated": {"graphs_per_s": value, "p50_s": _pct(lat, 0.5), "p99_s": _pct(lat, 0.99),
-                          "plain_graphs_per_s": x_plain, "speedup_vs_plain": value / x_plain},
+                          "plain_graphs_per_s": x_plain, "speedup_vs_plain": value / x_plain,
+                          "graphs_replay": graphs_main,
+                          "by_graphs_replay": {("on" if gm else "off"): {
+                              "graphs_per_s": R / sat[gm][1], "p50_s": _pct(sat[gm][0], 0.5),
+                              "p99_s": _pct(sat[gm][0], 0.99)} for gm in (False, True)}},
             "rates": rates,
             "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": int(in_bytes),
                     "d2h_bytes_per_step": int(out_bytes)},
@@ -592,6 +635,9 @@ def main():
     ap.add_argument("--tables", type=int, default=0, choices=[0, 1],
                     help="1: high-degree tables kept across passes and updated in place")
     ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--tune", action="store_true",
+                    help="run lc_autotune on the workload first and cache its choice (tuning.json)")
+    ap.add_argument("--no-tuning", action="store_true", help="ignore cached tunings")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -156,6 +156,23 @@ typedef struct {
                                with dealloc = the library's private pool (default) */
   lc_free_fn dealloc;
   void *alloc_ctx;          /* passed to alloc and dealloc */
+  int32_t bin_max_deg[9];   /* degree bins of the per-vertex kernels (the degree buckets of
+                               Section IV-C-2, whose thresholds the paper leaves open):
+                               bin k takes bin_max_deg[k-1] < deg <= bin_max_deg[k], rows
+                               above bin_max_deg[8] are "hubs" cut into hub_chunk-edge
+                               chunks.  0 = the default of that bin (8, 16, 32, 128, 256,
+                               512, 1024, 2048, 4096, which are also each bin's largest
+                               allowed value); equal neighbours leave a bin empty.  Values
+                               must be non-decreasing (LC_ERR_ARG otherwise).  Results do
+                               not depend on them; lc_autotune picks them by timing.
+                               opts.tables = 1 needs the defaults. */
+  int32_t hub_chunk;        /* edges per hub chunk; 0 = 2048; 256 .. 65536 */
+  int32_t graphs;           /* 1 = the passes of a LocalMovePasses call that repeat the same
+                               launches (all but a first pass from singletons and the last)
+                               are captured once per call into a CUDA graph and replayed,
+                               which removes most per-kernel launch costs on small graphs.
+                               Ignored with profile, event_cb or tables = 1.  Results are
+                               identical.  Default 0. */
 } lc_opts;
 
 /* Kernel classes timed when opts.profile = 1. */
@@ -208,6 +225,32 @@ LC_API void lc_default_opts(lc_opts *o);
  * the input.  A run whose levels shrink more slowly can need more (compare
  * lc_result.scratch_peak_bytes).  -1 for negative sizes or count < 1. */
 LC_API int64_t lc_scratch_estimate(int64_t n, int64_t nnz, int32_t count, const lc_opts *opts);
+
+/* Launch settings chosen by lc_autotune. */
+typedef struct {
+  int32_t bin_max_deg[9]; /* for lc_opts.bin_max_deg */
+  int32_t hub_chunk;      /* for lc_opts.hub_chunk */
+  int32_t graphs;         /* for lc_opts.graphs */
+  int32_t trials;         /* settings timed */
+  double ms_default;      /* median milliseconds of one call with the starting settings */
+  double ms_best;         /* ... with the chosen ones */
+} lc_tuning;
+
+/* Picks the degree-bin boundaries, hub chunk length and graph replay for a
+ * workload by timing them (the paper leaves its bucket thresholds open,
+ * Section IV-C-2; no setting changes a result).  Starting from opts (NULL:
+ * the defaults), it moves one setting at a time, runs lc_cluster (count = 1)
+ * or lc_cluster_batch (count graphs, as that call) `repeats` times after one
+ * untimed run, and keeps a change only if the median time falls.  Every
+ * candidate's labels are compared with those of the starting settings
+ * (LC_ERR_DEVICE if one differs, which would be a library fault).  Arguments
+ * as lc_cluster / lc_cluster_batch: graph_ptr, lambda_num and lambda_den are
+ * HOST arrays (count + 1, count, count entries); for count = 1 graph_ptr may
+ * be NULL.  opts.tables = 1 is rejected (LC_ERR_ARG).  Each trial is a full
+ * clustering, so the call takes about 2 * 15 * repeats clusterings. */
+LC_API int lc_autotune(const lc_csr *g, const int64_t *vertex_w, const int32_t *edge_w, int32_t count,
+                       const int64_t *graph_ptr, const int64_t *lambda_num, const int64_t *lambda_den,
+                       const lc_opts *opts, int32_t repeats, lc_tuning *out);
 
 /* Human-readable name of an LC_* code (static string). */
 LC_API const char *lc_strerror(int code);

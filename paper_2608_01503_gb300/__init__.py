@@ -21,6 +21,8 @@ Functions carry the C names:
   lc_server_*       the clustering service: submit host graphs, poll/wait
                     for results; Server wraps it as a context manager
   lc_scratch_estimate  device scratch a call is expected to need
+  lc_autotune       degree-bin boundaries, hub chunks and graph replay timed
+                    on a workload (cached in tuning.json by load/save_tuning)
   lc_release_memory    return the library pool's cached blocks to the device
   lc_strerror       name of an error code
 """
@@ -100,7 +102,8 @@ class _Opts(ctypes.Structure):
                 ("event_cb", _EventFn), ("event_ctx", ctypes.c_void_p),
                 ("symmetry", ctypes.c_int32), ("tables", ctypes.c_int32),
                 ("scratch_limit", ctypes.c_int64), ("alloc", _AllocFn), ("dealloc", _FreeFn),
-                ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc_ctx", ctypes.c_void_p), ("bin_max_deg", ctypes.c_int32 * 9),
+                ("hub_chunk", ctypes.c_int32), ("graphs", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
@@ -114,6 +117,12 @@ class _Result(ctypes.Structure):
                 ("scratch_peak_bytes", ctypes.c_int64)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("bin_max_deg", ctypes.c_int32 * 9), ("hub_chunk", ctypes.c_int32),
+                ("graphs", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double)]
+
+
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("opts", _Opts)]
@@ -125,7 +134,7 @@ EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
            "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
            "lc_server_wait", "lc_server_destroy", "lc_server_cancel", "lc_release_memory",
-           "lc_scratch_estimate"]
+           "lc_scratch_estimate", "lc_autotune"]
 
 
 def library_path() -> str:
@@ -166,6 +175,8 @@ def load(build_if_missing: bool = True):
     lib.lc_release_memory.restype = ctypes.c_int
     lib.lc_scratch_estimate.argtypes = [i64, i64, i32, opts]
     lib.lc_scratch_estimate.restype = ctypes.c_int64
+    lib.lc_autotune.argtypes = [csr, P, P, i32, P, P, P, opts, i32, ctypes.POINTER(_Tuning)]
+    lib.lc_autotune.restype = ctypes.c_int
     srv = ctypes.c_void_p
     lib.lc_server_default_config.argtypes = [ctypes.POINTER(_ServerConfig)]
     lib.lc_server_default_config.restype = None
@@ -205,6 +216,9 @@ class Options:
     tables: int = 0  # 1: high-degree tables kept across passes and updated in place
     allocator: str = "torch"  # device scratch from PyTorch's caching allocator, or "library"
                               # for liblc's private pool
+    bins: tuple = ()  # upper degrees of the 9 shared-memory bins (0 or missing = default)
+    hub_chunk: int = 0  # edges per hub chunk (0 = default)
+    graphs: bool = False  # replay the repeated passes of each LocalMovePasses call from a CUDA graph
 
 
 def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
@@ -225,6 +239,13 @@ def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     c.symmetry = int(o.symmetry)
     c.scratch_limit = int(o.scratch_limit)
     c.tables = int(o.tables)
+    bins = list(o.bins) + [0] * (9 - len(o.bins))
+    if len(bins) != 9:
+        raise ValueError("bins holds at most 9 upper degrees")
+    for k in range(9):
+        c.bin_max_deg[k] = int(bins[k])
+    c.hub_chunk = int(o.hub_chunk)
+    c.graphs = int(bool(o.graphs))
     c.stream = stream
     if event_fn is not None:
         c.event_cb = event_fn
@@ -498,6 +519,72 @@ def lc_scratch_estimate(n: int, nnz: int, count: int = 1, opts: Options | None =
     lc_cluster_batch needs for n vertices and nnz stored edges (bytes)."""
     c = _c_opts(opts, None)
     return int(load().lc_scratch_estimate(int(n), int(nnz), int(count), ctypes.byref(c)))
+
+
+def lc_autotune(row_ptr, col, ew, vw, lambda_num, lambda_den, graph_ptr=None,
+                opts: Options | None = None, repeats: int = 3, stream=None) -> dict:
+    """Times the degree-bin boundaries, hub chunk length and graph replay on
+    this workload (one graph, or a packed batch with host graph_ptr and
+    per-graph lambda sequences) and returns the fastest setting, which gives
+    identical results: {"bins", "hub_chunk", "graphs", "trials",
+    "ms_default", "ms_best"}.  tuned_options() turns it into Options."""
+    import torch
+
+    lib = load()
+    n = row_ptr.numel() - 1
+    csr = _Csr(n, col.numel(), _dev(row_ptr, torch.int64, "row_ptr"), _dev(col, torch.int32, "col"))
+    if graph_ptr is None:
+        count, gp = 1, None
+        ln = np.array([lambda_num], dtype=np.int64)
+        ld = np.array([lambda_den], dtype=np.int64)
+    else:
+        gp = np.ascontiguousarray(graph_ptr, dtype=np.int64)
+        ln = np.ascontiguousarray(lambda_num, dtype=np.int64)
+        ld = np.ascontiguousarray(lambda_den, dtype=np.int64)
+        count = int(gp.shape[0] - 1)
+    c = _c_opts(opts, _stream_handle(stream))
+    t = _Tuning()
+    rc = lib.lc_autotune(ctypes.byref(csr), _dev(vw, torch.int64, "vw"), _dev(ew, torch.int32, "ew"), count,
+                         gp.ctypes.data if gp is not None else None, ln.ctypes.data, ld.ctypes.data,
+                         ctypes.byref(c), int(repeats), ctypes.byref(t))
+    _check(rc)
+    return {"bins": list(t.bin_max_deg), "hub_chunk": t.hub_chunk, "graphs": bool(t.graphs),
+            "trials": t.trials, "ms_default": t.ms_default, "ms_best": t.ms_best}
+
+
+def tuned_options(tuning: dict | None, **kw) -> Options:
+    """Options carrying a tuning (lc_autotune / load_tuning); None: defaults."""
+    if tuning:
+        kw.setdefault("bins", tuple(tuning["bins"]))
+        kw.setdefault("hub_chunk", int(tuning["hub_chunk"]))
+        kw.setdefault("graphs", bool(tuning["graphs"]))
+    return Options(**kw)
+
+
+TUNING_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
+def load_tuning(key: str, path: str = TUNING_CACHE) -> dict | None:
+    """A cached tuning for `key` (a workload and device name), or None."""
+    import json
+
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f).get(key)
+
+
+def save_tuning(key: str, tuning: dict, path: str = TUNING_CACHE) -> None:
+    import json
+
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[key] = tuning
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+        f.write("\n")
 
 
 def lc_release_memory() -> None:

@@ -137,6 +137,7 @@ struct Level {
 struct Run {
   cudaStream_t s;
   lc_opts o;
+  BinPlan plan = default_bin_plan();
   Method m;
   lc_result *res;  // [G]
   int G = 1;
@@ -151,6 +152,8 @@ struct Run {
   int64_t *W = nullptr, *delta = nullptr, *bound = nullptr, *off = nullptr, *scan64 = nullptr;
   uint8_t *M = nullptr, *E = nullptr;
   AbRec *ab = nullptr;
+  uint32_t *inL = nullptr;    // afterburner candidate bitmap
+  int32_t *ab_list = nullptr; // afterburner candidates by group
   int2 *upd_list = nullptr;
   unsigned long long *gtab = nullptr;
   long long *gself = nullptr;
@@ -163,8 +166,39 @@ struct Run {
   uint8_t *keep = nullptr;
   GraphStats *st = nullptr;
   std::vector<long long> hT, hV, hsw2;
+  std::vector<cudaGraphExec_t> execs;  // captured passes (opts.graphs), freed with the call
   explicit Run(const lc_opts &o_) : s((cudaStream_t)o_.stream), o(o_), ar((cudaStream_t)o_.stream, o_) {}
+  Run(const Run &) = delete;
+  ~Run() {
+    if (execs.empty()) return;
+    cudaStreamSynchronize(s);  // replays finished before their graphs go
+    for (cudaGraphExec_t e : execs) cudaGraphExecDestroy(e);
+    cudaGetLastError();
+  }
 };
+
+// A stream owned by the library to capture on (the caller's stream may be
+// the legacy default stream, which cannot be captured); one per host thread
+// and device.  Captured work is only recorded there and runs, as a graph, on
+// the call's own stream.
+static cudaStream_t capture_stream() {
+  struct Streams {
+    std::vector<cudaStream_t> s;
+    ~Streams() {
+      for (cudaStream_t x : s)
+        if (x) cudaStreamDestroy(x);
+    }
+  };
+  thread_local Streams st;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if ((int)st.s.size() <= dev) st.s.resize(dev + 1, nullptr);
+  if (!st.s[dev] && cudaStreamCreateWithFlags(&st.s[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    st.s[dev] = nullptr;
+  }
+  return st.s[dev];
+}
 
 static int alloc_per_graph(Run &r) {
   const int G = r.G;
@@ -206,6 +240,8 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   LC_TRY(r.ar.get(&r.W, n0));
   LC_TRY(r.ar.get(&r.delta, n0));
   LC_TRY(r.ar.get(&r.ab, n0));
+  LC_TRY(r.ar.get(&r.inL, (n0 + 31) / 32));
+  LC_TRY(r.ar.get(&r.ab_list, n0));
   LC_TRY(r.ar.get(&r.bound, n0 + 1));
   LC_TRY(r.ar.get(&r.off, n0 + 1));
   LC_TRY(r.ar.get(&r.scan64, scan_scratch(n0 + 1)));
@@ -219,6 +255,27 @@ static int alloc_scratch(Run &r, int64_t n0, int64_t nnz0) {
   return LC_OK;
 }
 
+// The degree bins of a call from its options (zeros take the defaults).
+static int resolve_plan(const lc_opts &o, BinPlan *out) {
+  BinPlan p = default_bin_plan();
+  int64_t prev = 0;
+  for (int k = 0; k < kBins - 1; ++k) {
+    const int64_t v = o.bin_max_deg[k];
+    if (v < 0 || v > kBinMaxDeg[k]) return LC_ERR_ARG;
+    if (v > 0) p.max_deg[k] = v;
+    if (p.max_deg[k] < prev) return LC_ERR_ARG;
+    prev = p.max_deg[k];
+  }
+  if (o.hub_chunk != 0) {
+    if (o.hub_chunk < 256 || o.hub_chunk > 65536) return LC_ERR_ARG;
+    p.hub_chunk = o.hub_chunk;
+  }
+  // kept tables share the shared-memory layout of the default bins (tab_cap)
+  if (o.tables == 1 && !is_default_plan(p)) return LC_ERR_ARG;
+  *out = p;
+  return LC_OK;
+}
+
 // Bytes the allocations above, prepare() and level0() request for G_0 of a
 // call on `G` graphs (kept in step with them), and those of one level's
 // bins, hub plan, parameters, dense ids and coarse graph (bins_for,
@@ -229,14 +286,15 @@ static int64_t level0_scratch_bytes(int64_t n0, int64_t nnz0, int64_t G, int tab
   b += 11 * 4 * n;                                           // C .. movers
   if (tables == 1) b += 2 * 4 * n + 8 * upd_list_size(n0, nnz0);
   b += 4 * scan_scratch(big);                                // scan32
-  b += 3 * 8 * n + (int64_t)sizeof(AbRec) * n;               // W, delta, ab (and bound, off below)
+  b += 2 * 8 * n + (int64_t)sizeof(AbRec) * n;               // W, delta, ab
+  b += 4 * ((n0 + 31) / 32 + 1) + 4 * n;                     // inL, ab_list
   b += 2 * 8 * (n0 + 1) + 8 * scan_scratch(n0 + 1) + 2 * n;  // bound, off, scan64, M, E
   b += 8 * (2 * nnz0 > 0 ? 2 * nnz0 : 1);                    // gtab
   if (G > 1) b += 8 * n + 8 * (G + 1) + 4 * n;               // gself, graph_ptr, gid
   return b + (int64_t)sizeof(Scalars) + (int64_t)sizeof(GraphStats);
 }
-static int64_t level_bytes(int64_t n, int64_t nnz, int64_t G) {
-  const int64_t hubs = nnz / kHubDeg + 1, chunks = nnz / kHubChunk + hubs;
+static int64_t level_bytes(int64_t n, int64_t nnz, int64_t G, const BinPlan &p) {
+  const int64_t hubs = nnz / (p.hub_min() + 1) + 1, chunks = nnz / p.hub_chunk + hubs;
   return 4 * n + 4 * (kBins + 1) + 40 * chunks + 36 * hubs  // bins, hub plan
          + (int64_t)sizeof(GraphParam) * G                   // upload_params
          + 4 * n + (G > 1 ? 4 * n : 0)                      // Cd, next level's gid
@@ -244,16 +302,18 @@ static int64_t level_bytes(int64_t n, int64_t nnz, int64_t G) {
 }
 
 int64_t cluster_footprint(int64_t n, int64_t nnz, int count, const lc_opts &o) {
+  BinPlan p;
+  if (resolve_plan(o, &p) != LC_OK) p = default_bin_plan();
   // level 0 exactly, then coarse levels whose sizes sum to at most G_0's
-  return level0_scratch_bytes(n, nnz, count, o.tables) + 2 * level_bytes(n, nnz, count) + (1 << 20);
+  return level0_scratch_bytes(n, nnz, count, o.tables) + 2 * level_bytes(n, nnz, count, p) + (1 << 20);
 }
 
 // Degree bins of a level, and the chunk plan of its hub bin (rows longer
-// than the largest shared-memory bin are cut into kHubChunk-edge chunks).
+// than the last shared-memory bin are cut into chunks of the plan's hub_chunk edges).
 static int bins_for(Run &r, Level &L) {
   LC_TRY(r.ar.get(&L.bins.lists, L.g.n));
   LC_TRY(r.ar.get(&L.bins.offs, kBins + 1));
-  build_bins(L.g, L.bins, r.scan32, r.s);
+  build_bins(L.g, r.plan, L.bins, r.scan32, r.s);
   int32_t h[kBins + 1];
   LC_CK(cudaMemcpyAsync(h, L.bins.offs, sizeof(h), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
@@ -273,10 +333,11 @@ static int bins_for(Run &r, Level &L) {
     std::vector<int64_t> e0, e1;
     for (int k = 0; k < H; ++k) {
       c0[k] = (int32_t)hub_of.size();
-      for (int64_t b = hrows[2 * k]; b < hrows[2 * k + 1]; b += kHubChunk) {
+      const int64_t ch = r.plan.hub_chunk;
+      for (int64_t b = hrows[2 * k]; b < hrows[2 * k + 1]; b += ch) {
         hub_of.push_back(k);
         e0.push_back(b);
-        e1.push_back(b + kHubChunk < hrows[2 * k + 1] ? b + kHubChunk : hrows[2 * k + 1]);
+        e1.push_back(b + ch < hrows[2 * k + 1] ? b + ch : hrows[2 * k + 1]);
       }
     }
     const int Q = (int)hub_of.size();
@@ -350,6 +411,10 @@ static PassArgs pass_args(Run &r, const Level &L) {
   a.Cprev = r.Cprev;
   a.dirty = r.dirty;
   a.dirty_list = r.dirty_list;
+  a.hub_min = r.plan.hub_min();
+  a.inL = r.inL;
+  a.ab_list = r.ab_list;
+  set_ab_groups(a, L.bins, r.plan);
   return a;
 }
 
@@ -396,6 +461,42 @@ static int emit_pass_event(Run &r, const Level &L, int level, int phase, int pas
   return LC_OK;
 }
 
+// Records one pass of Algorithm 2 that is neither a first pass from
+// singletons nor the last of its call (move step, best-of test, afterburner,
+// update; the temperature comes from the device schedule) into an
+// executable CUDA graph.  counts: kernels per class in one replay.
+static int capture_pass(Run &r, Level &L, const PassArgs &a, const ApplyScratch &w, cudaGraphExec_t *out,
+                        int64_t counts[LC_K_COUNT]) {
+  *out = nullptr;
+  cudaStream_t cs = capture_stream();
+  if (!cs) return LC_ERR_CUDA;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return LC_ERR_CUDA;
+  }
+  for (int k = 0; k < LC_K_COUNT; ++k) counts[k] = 0;
+  launch_pass_begin(r.sc, cs, 1);
+  counts[LC_K_MOVE] += launch_move(a, L.bins, cs);
+  counts[LC_K_APPLY] += launch_graph_sums(a, cs) + launch_bestof(a, r.C_out, cs);
+  counts[LC_K_AFTERBURNER] += launch_afterburner(a, L.bins, cs);
+  counts[LC_K_APPLY] += launch_apply(a, w, cs) + 1;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (e != cudaSuccess || !g) {
+    cudaGetLastError();
+    return LC_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return LC_ERR_CUDA;
+  }
+  r.execs.push_back(*out);
+  return LC_OK;
+}
+
 // Algorithm 2: `pass_limit` synchronous passes from r.C for the graphs with
 // active[g]; leaves C_out (the best clustering seen, strict improvement) in
 // r.C_out and Phi(C_out) per graph in r.phi_out.
@@ -426,11 +527,43 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   a.upd_list = tables ? r.upd_list : nullptr;
   // one graph: the final objective is updated from the last pass (see below)
   const bool incremental = r.G == 1;
+  // opts.graphs: the repeated passes replay one captured pass; every pass
+  // then reads its temperature from the device schedule
+  bool capture = r.o.graphs == 1 && !r.prof.on && !(r.o.event_cb && r.G == 1) && !tables &&
+                 r.o.symmetry == 0;
+  if (capture) {
+    int tab[16][2];
+    for (int k = 0; k < 16; ++k) {
+      tab[k][0] = r.o.phi_num[k];
+      tab[k][1] = r.o.phi_den[k];
+    }
+    LC_CK(cudaMemcpyAsync(r.sc->phi_tab, tab, sizeof(tab), cudaMemcpyHostToDevice, r.s));
+    LC_CK(cudaMemsetAsync(&r.sc->pass_idx, 0, sizeof(int), r.s));
+    a.phi_live = r.sc->phi_live;
+  }
+  cudaGraphExec_t exec = nullptr;
+  int64_t exec_counts[LC_K_COUNT];
   for (int i = 1; i <= r.o.pass_limit; ++i) {
     a.phi_n = r.o.phi_num[i - 1];
     a.phi_d = r.o.phi_den[i - 1];
-    launch_pass_begin(r.sc, r.s);
     const bool last = i == r.o.pass_limit;
+    if (capture && !last && !(i == 1 && singleton)) {
+      PassArgs ga = a;  // a repeated pass lists no movers and builds no tables
+      ga.movers = nullptr;
+      ga.tab_build = 0;
+      if (!exec && capture_pass(r, L, ga, w, &exec, exec_counts) != LC_OK) {
+        // capture is an optimisation only: the same pass, launched directly
+        capture = exec != nullptr;
+      }
+      if (exec) {
+        LC_CK(cudaGraphLaunch(exec, r.s));
+        for (int k = 0; k < LC_K_COUNT; ++k) r.res->kernel_launches[k] += exec_counts[k];
+        r.res->passes_total++;
+        r.res->edges_local_move += nnz;
+        continue;
+      }
+    }
+    launch_pass_begin(r.sc, r.s, a.phi_live ? 1 : 0);
     a.movers = incremental && last ? r.movers : nullptr;  // listed by this pass's update step
     if (incremental && last) {
       r.prof.begin(LC_K_OBJECTIVE);
@@ -682,6 +815,7 @@ static int contract_level(Run &r, Level &L, Level &N, int level) {
 
 static int check_opts(const lc_opts &o) {
   if (o.pass_limit < 0 || o.pass_limit > 16) return LC_ERR_ARG;
+  if (o.graphs < 0 || o.graphs > 1) return LC_ERR_ARG;
   for (int i = 0; i < o.pass_limit; ++i)
     if (o.phi_den[i] <= 0 || o.phi_num[i] < 0 || o.phi_num[i] > o.phi_den[i]) return LC_ERR_ARG;
   if (o.eps_num <= 0 || o.eps_den <= 0) return LC_ERR_ARG;
@@ -904,6 +1038,7 @@ static int begin_call(Run &r, const lc_opts *opts, lc_result *res, int G) {
   r.G = G;
   memset(res, 0, sizeof(lc_result) * (size_t)G);
   LC_TRY(check_opts(r.o));
+  LC_TRY(resolve_plan(r.o, &r.plan));
   r.ar.limit = r.o.scratch_limit;
   configure_device();
   r.prof.on = r.o.profile != 0;

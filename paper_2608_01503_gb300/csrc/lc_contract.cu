@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
   });
 }
 
-// Hub rows: one block per chunk of kHubChunk edges.
+// Hub rows: one block per chunk of the level's hub plan.
 __global__ void __launch_bounds__(kHubThreads) k_insert_hub(InsertArgs a, Hubs hub) {
   const int c = blockIdx.x;
   const int32_t v = hub.vtx[hub.hub_of[c]];

@@ -20,7 +20,8 @@ constexpr int32_t kEmpty = -2;  // D[v]: move v to a new empty cluster
 constexpr unsigned long long kEmptySlot = 0ull;
 constexpr int kMaxLevels = 256;
 
-// Degree bins of the per-vertex kernels.  A vertex of degree d is handled by
+// Degree bins of the per-vertex kernels.  By default (the boundaries are
+// runtime parameters, see BinPlan) a vertex of degree d is handled by
 //   bin 0: d <= 8       one thread (aggregation in registers)
 //   bin 1: d <= 16      16 lanes, one neighbour per lane (2 vertices per warp)
 //   bin 2: d <= 32      one warp, one neighbour per lane
@@ -30,7 +31,7 @@ constexpr int kMaxLevels = 256;
 //   bin 6: d <= 1024    128 threads, shared table of 2048 slots
 //   bin 7: d <= 2048    256 threads, shared table of 4096 slots
 //   bin 8: d <= 4096    256 threads, shared table of 6144 slots (load <= 2/3)
-//   bin 9: d >  4096    "hubs": the row is cut into chunks of kHubChunk edges
+//   bin 9: d >  4096    "hubs": the row is cut into chunks of 2048 edges
 //                       processed by independent blocks, aggregation in the
 //                       vertex's region of the global table (2d slots), then
 //                       one finalize step per hub
@@ -39,14 +40,36 @@ constexpr int kMaxLevels = 256;
 // Kernels without tables launch once over a contiguous range of bins.
 constexpr int kBins = 10;
 constexpr int kHubBin = kBins - 1;
+// The largest degree each bin's kernel can take (its registers or shared
+// table), which is also the default bin boundary.
 constexpr int64_t kBinMaxDeg[kBins - 1] = {8, 16, 32, 128, 256, 512, 1024, 2048, 4096};
 constexpr int kWarpBinWarps = 8;    // warps per block in the warp-table bins
 constexpr int kHubThreads = 256;
-constexpr int kHubChunk = 2048;     // edges per hub chunk
-constexpr int64_t kHubDeg = 4096;   // rows longer than this are hubs (bin 9)
+constexpr int kHubChunk = 2048;     // edges per hub chunk (default)
 constexpr int kBin8Slots = 6144;    // shared table of bin 8
 constexpr int64_t kTabMinDeg = 256; // kept tables (opts.tables): vertices of degree above this
 constexpr int kUpdChunk = 256;      // edges per chunk of a mover's row in the table update
+
+// Degree bins of one call (lc_opts.bin_max_deg / hub_chunk): bin k takes
+// max_deg[k-1] < deg <= max_deg[k] (bin 0 from degree 0), the hub bin the
+// rows above max_deg[kBins - 2], in chunks of hub_chunk edges.  Every
+// max_deg[k] <= kBinMaxDeg[k], so each vertex fits its kernel.
+struct BinPlan {
+  int64_t max_deg[kBins - 1];
+  int64_t hub_chunk;
+  int64_t hub_min() const { return max_deg[kBins - 2]; }  // hubs: deg > hub_min()
+};
+inline BinPlan default_bin_plan() {
+  BinPlan p;
+  for (int k = 0; k < kBins - 1; ++k) p.max_deg[k] = kBinMaxDeg[k];
+  p.hub_chunk = kHubChunk;
+  return p;
+}
+inline bool is_default_plan(const BinPlan &p) {
+  for (int k = 0; k < kBins - 1; ++k)
+    if (p.max_deg[k] != kBinMaxDeg[k]) return false;
+  return p.hub_chunk == kHubChunk;
+}
 
 // Slots of the kept table of a vertex of degree d, in shared memory and in
 // its region gtab[2 rp[v], 2 rp[v+1]) of the global table alike: 2d (load at
@@ -124,7 +147,19 @@ struct Scalars {
   long long dphi_edges;  // movers' edges read for d_in, summed over the call
   int n_movers;          // entries of PassArgs::movers
   int pad3;
+  int ab_count[8];       // candidates listed per afterburner group in this pass
+  // device-side temperature schedule (graph replays): k_pass_begin loads
+  // phi_live from phi_tab[pass_idx] and advances pass_idx
+  int pass_idx;
+  int phi_live[2];
+  int pad5;
+  int phi_tab[16][2];
 };
+
+// The afterburner's launches group the degree bins (one kernel each):
+// bin 0, bin 1, bins 2-4, bins 5-6, bins 7-8; hubs go by chunks.
+constexpr int kAbGroups = 5;
+constexpr int kAbFirstBin[kAbGroups + 1] = {0, 1, 2, 5, 7, 9};
 
 // ------------------------------------------------------------------ hashes
 

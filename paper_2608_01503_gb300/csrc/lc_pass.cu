@@ -67,8 +67,9 @@ __device__ __forceinline__ void decide(const PassArgs &a, const GraphParam &P, i
     best = kEmpty;
     gbest = 0;
   }
-  const bool inL = best != kNone &&
-                   (__int128)a.phi_d * gbest >= (__int128)(a.phi_d - a.phi_n) * (__int128)gC;
+  const int32_t pn = a.phi_live ? a.phi_live[0] : a.phi_n;
+  const int32_t pd = a.phi_live ? a.phi_live[1] : a.phi_d;
+  const bool inL = best != kNone && (__int128)pd * gbest >= (__int128)(pd - pn) * (__int128)gC;
   if (inL) {
     a.D[v] = best;
     a.delta[v] = gbest - gC;
@@ -475,9 +476,13 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
                                                    int64_t count) {
   extern __shared__ uint32_t smem_tab[];
   const SplitTab tab{smem_tab, reinterpret_cast<int32_t *>(smem_tab + SLOTS)};
-  __shared__ long long rs[GS / 32];
-  __shared__ long long rg[GS / 32];
-  __shared__ int32_t rx[GS / 32];
+  // per-warp partials, double-buffered by vertex parity: thread 0 combines
+  // vertex i's while the other threads already insert vertex i + 1, and the
+  // buffer is written again only after two more barriers (vertex i + 2)
+  __shared__ long long rs[2][GS / 32];
+  __shared__ long long rg[2][GS / 32];
+  __shared__ int32_t rx[2][GS / 32];
+  int par = 0;
   long long cntL = 0, phi = 0;
   for (int s = threadIdx.x; s < SLOTS; s += GS) {
     tab.key[s] = 0u;
@@ -505,17 +510,19 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     group_argmax<32>(gb, xb);
     self = warp_sum(self);
     if ((threadIdx.x & 31) == 0) {
-      rg[threadIdx.x >> 5] = gb;
-      rx[threadIdx.x >> 5] = xb;
-      rs[threadIdx.x >> 5] = self;
+      rg[par][threadIdx.x >> 5] = gb;
+      rx[par][threadIdx.x >> 5] = xb;
+      rs[par][threadIdx.x >> 5] = self;
     }
+    // the table is read and reset by every thread past this barrier, so the
+    // next vertex may start inserting at once
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int w = 1; w < GS / 32; ++w) {
-        self += rs[w];
-        if (better(rg[w], rx[w], gb, xb)) {
-          gb = rg[w];
-          xb = rx[w];
+        self += rs[par][w];
+        if (better(rg[par][w], rx[par][w], gb, xb)) {
+          gb = rg[par][w];
+          xb = rx[par][w];
         }
       }
       // the barrier above made every thread's copied slots visible
@@ -524,7 +531,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
       add_self(a, v, gC, phi);
       decide(a, P, v, gC, xb, gb, cntL);
     }
-    __syncthreads();
+    par ^= 1;
   }
   flush_block_sum(cntL, &a.sc->count_L);
   flush_block_sum(phi, &a.phi_acc[0]);
@@ -672,18 +679,46 @@ __global__ void k_hub_decide(PassArgs a, int first) {
 // neighbour gathers (one 16-byte load each).  The bucket of Section IV-A-1,
 // floor(eps_den * delta / (eps_num * Lambda)), needs a 128-bit division; it
 // is done here, one thread per vertex, off the aggregation kernels.
-// It also sums the candidates' degrees (the afterburner's edge work) into
+// It also writes the candidate bitmap (one ballot per warp: a warp covers 32
+// consecutive, aligned ids), lists the candidates below the hub degree by
+// afterburner group (warp-aggregated appends; the order inside a list does
+// not matter, each candidate's sum is independent of the others), clears
+// M, and sums the candidates' degrees (the afterburner's edge work) into
 // sc->cand_edges for the algorithmic-byte count of the profile.
-__global__ void k_ab_prep(PassArgs a) {
+__global__ void __launch_bounds__(256) k_ab_prep(PassArgs a) {
   long long cand = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.g.n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    AbRec r;
-    r.C = a.C[v];
-    r.D = a.D[v];
-    r.q = r.D != kNone ? eps_bucket(a.m, a.gp[graph_of(a, (int32_t)v)].Lam, a.delta[v]) : 0;
-    a.ab[v] = r;
-    if (r.D != kNone) cand += a.g.rp[v + 1] - a.g.rp[v];
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.g.n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    const int64_t w0 = base + (threadIdx.x & ~31);  // first id of this warp
+    bool isc = false;
+    int grp = -1;
+    if (v < a.g.n) {
+      AbRec r;
+      r.C = a.C[v];
+      r.D = a.D[v];
+      isc = r.D != kNone;
+      r.q = isc ? eps_bucket(a.m, a.gp[graph_of(a, (int32_t)v)].Lam, a.delta[v]) : 0;
+      a.ab[v] = r;
+      a.M[v] = 0;  // survivors are set by the afterburner kernels
+      if (isc) {
+        const int64_t deg = a.g.rp[v + 1] - a.g.rp[v];
+        cand += deg;
+        for (int k = 0; k < kAbGroups && grp < 0; ++k)
+          if (deg <= a.ab_max[k]) grp = k;  // hubs stay unlisted (grp -1)
+      }
+    }
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, isc);
+    if (lane == 0 && w0 < a.g.n) a.inL[w0 >> 5] = bits;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, grp);
+    if (grp >= 0) {
+      const int leader = __ffs(peers) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(&a.sc->ab_count[grp], __popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+      a.ab_list[a.ab_off[grp] + pos] = (int32_t)v;
+    }
   }
   flush_block_sum(cand, &a.sc->cand_edges);
 }
@@ -736,10 +771,15 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
         w[k] = __ldg(ew + e);
       }
     }
+    // only candidates matter (Algorithm 3): test the bitmap first, gather
+    // the 16-byte record of candidate neighbours only
+    uint32_t word[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) word[k] = u[k] >= 0 ? __ldg(a.inL + (u[k] >> 5)) : 0u;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       rec[k].D = kNone;
-      if (u[k] >= 0) rec[k] = a.ab[u[k]];
+      if ((word[k] >> (u[k] & 31)) & 1u) rec[k] = a.ab[u[k]];
     }
     bool need[U];
 #pragma unroll
@@ -770,26 +810,22 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
 
 // For each candidate v: delta_v adjusted by every adjacent candidate u that
 // precedes v in the order; v survives iff the adjusted delta is >= 0.
+// list / *count: the candidates of one group, listed by k_ab_prep.
 template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 4)
-    k_afterburner(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
+    k_afterburner(PassArgs a, const int32_t *__restrict__ list, const int *__restrict__ count_ptr) {
   constexpr int U = 4;
   long long cntM = 0;
   const int r = Grp<GS>::rank();
+  const int64_t count = *count_ptr;
   if constexpr (GS > 32) {
-    // block per vertex: non-candidates are skipped by the whole block, and
-    // the per-warp sums alternate between two buffers, so one barrier per
-    // candidate suffices (the next candidate's barrier orders thread 0's
-    // reads before the buffer is written again)
+    // block per candidate: the per-warp sums alternate between two buffers,
+    // so one barrier per candidate suffices (the next candidate's barrier
+    // orders thread 0's reads before the buffer is written again)
     __shared__ long long rs[2][GS / 32];
     int par = 0;
     for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
       const int32_t v = list[i];
-      const int32_t Dv = a.D[v];
-      if (Dv == kNone) {
-        if (threadIdx.x == 0) a.M[v] = 0;
-        continue;
-      }
       const AbCtx c = ab_ctx(a, v);
       long long acc = warp_sum(ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r));
       if ((threadIdx.x & 31) == 0) rs[par][threadIdx.x >> 5] = acc;
@@ -807,15 +843,14 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 
     __shared__ long long rs[1];
     for_each_vertex<GS>(count, [&](int64_t i, bool active) {
       const int32_t v = active ? list[i] : 0;
-      const int32_t Dv = active ? a.D[v] : kNone;
       long long acc = 0;
-      if (Dv != kNone) {
+      if (active) {
         const AbCtx c = ab_ctx(a, v);
         acc = ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r);
       }
       acc = Grp<GS>::sum(acc, rs);
       if (active && r == 0) {
-        const bool keep = Dv != kNone && a.delta[v] + acc >= 0;
+        const bool keep = a.delta[v] + acc >= 0;
         a.M[v] = keep;
         cntM += keep;
       }
@@ -1147,7 +1182,7 @@ __global__ void k_apply(PassArgs a, uint8_t *__restrict__ E) {
         if (a.upd_list || a.movers) {
           const int64_t deg = a.g.rp[v + 1] - a.g.rp[v];
           if (a.upd_list) nch = (int)((deg + kUpdChunk - 1) / kUpdChunk);
-          listed = a.movers && deg <= kHubDeg;  // hubs: k_hub_delta_in
+          listed = a.movers && deg <= a.hub_min;  // hubs: k_hub_delta_in
         }
         atomicAdd((unsigned long long *)&a.W[Cv], (unsigned long long)(-wv));
         if (Dv >= 0) {
@@ -1282,7 +1317,13 @@ __global__ void k_graph_sums(PassArgs a) {
 
 // ----------------------------------------------------------- best-of
 
-__global__ void k_pass_begin(Scalars *sc) {
+__global__ void k_pass_begin(Scalars *sc, int advance) {
+  if (advance) {
+    const int i = sc->pass_idx++;
+    sc->phi_live[0] = sc->phi_tab[i & 15][0];
+    sc->phi_live[1] = sc->phi_tab[i & 15][1];
+  }
+  for (int g = 0; g < kAbGroups; ++g) sc->ab_count[g] = 0;
   sc->count_L = 0;
   sc->count_M = 0;
   sc->empty_movers = 0;
@@ -1389,11 +1430,11 @@ void configure_kernels() {
                        block_table_bytes(6144));
 }
 
-void build_bins(const LevelGraph &g, Bins &b, int32_t *scan_tmp, cudaStream_t s) {
+void build_bins(const LevelGraph &g, const BinPlan &plan, Bins &b, int32_t *scan_tmp, cudaStream_t s) {
   cudaMemsetAsync(b.offs, 0, sizeof(int32_t), s);
   int64_t lo = -1;
   for (int k = 0; k < kBins; ++k) {
-    const int64_t hi = k < kBins - 1 ? kBinMaxDeg[k] : INT64_MAX;
+    const int64_t hi = k < kBins - 1 ? plan.max_deg[k] : INT64_MAX;
     scan_apply<int32_t>(g.n, BinFlag{g.rp, lo, hi}, BinEmit{b.lists, b.offs + k}, scan_tmp, s);
     k_bin_next_offset<<<1, 1, 0, s>>>(b.offs, k, scan_tmp + scan_tiles(g.n));
     lo = hi;
@@ -1514,14 +1555,34 @@ int launch_table_pass(const PassArgs &a, const Bins &b, cudaStream_t s) {
   return n;
 }
 
+// One afterburner group: its kernel over the candidates k_ab_prep listed
+// (grid sized for the whole group; surplus blocks find no work).
+template <int GS>
+static int launch_ab_group(const PassArgs &a, const Bins &b, int g, cudaStream_t s) {
+  const BinRange r = bin_range(b, kAbFirstBin[g], kAbFirstBin[g + 1] - 1);
+  if (r.count <= 0) return 0;
+  const int threads = GS > 32 ? GS : 256;
+  const int per_block = GS > 32 ? 1 : threads / GS;
+  k_afterburner<GS><<<blocks_for(r.count, per_block), threads, 0, s>>>(a, a.ab_list + a.ab_off[g],
+                                                                        &a.sc->ab_count[g]);
+  return 1;
+}
+
+void set_ab_groups(PassArgs &a, const Bins &b, const BinPlan &plan) {
+  for (int g = 0; g < kAbGroups; ++g) {
+    a.ab_off[g] = b.list[kAbFirstBin[g]] - b.list[0];
+    a.ab_max[g] = plan.max_deg[kAbFirstBin[g + 1] - 1];
+  }
+}
+
 int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s) {
   int n = 1;
   k_ab_prep<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
-  n += launch_vertex_kernel<1>(k_afterburner<1>, a, bin_range(b, 0, 0), s);
-  n += launch_vertex_kernel<16>(k_afterburner<16>, a, bin_range(b, 1, 1), s);
-  n += launch_vertex_kernel<32>(k_afterburner<32>, a, bin_range(b, 2, 4), s);
-  n += launch_vertex_kernel<128>(k_afterburner<128>, a, bin_range(b, 5, 6), s);
-  n += launch_vertex_kernel<512>(k_afterburner<512>, a, bin_range(b, 7, 8), s);
+  n += launch_ab_group<1>(a, b, 0, s);
+  n += launch_ab_group<16>(a, b, 1, s);
+  n += launch_ab_group<32>(a, b, 2, s);
+  n += launch_ab_group<128>(a, b, 3, s);
+  n += launch_ab_group<512>(a, b, 4, s);
   if (a.hub.H > 0) {
     k_hub_afterburner<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     k_hub_ab_final<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a);
@@ -1716,7 +1777,7 @@ int launch_apply(const PassArgs &a, const ApplyScratch &w, cudaStream_t s) {
   return 10;
 }
 
-void launch_pass_begin(Scalars *sc, cudaStream_t s) { k_pass_begin<<<1, 1, 0, s>>>(sc); }
+void launch_pass_begin(Scalars *sc, cudaStream_t s, int advance) { k_pass_begin<<<1, 1, 0, s>>>(sc, advance); }
 
 int launch_graph_sums(const PassArgs &a, cudaStream_t s) {
   if (!a.gself) return 0;

@@ -25,6 +25,7 @@ struct PassArgs {
   Scalars *sc;
   unsigned long long *gtab;  // clean global hash scratch, >= 2 nnz slots
   int32_t phi_n, phi_d;      // temperature of this pass
+  const int *phi_live;       // non-null: the temperature is sc->phi_live (graph replays)
   Hubs hub;                  // chunk plan of the hub bin of this level
   // kept tables: each vertex's S(v, .) in its gtab region (tab_cap slots)
   int32_t tab_build;         // this aggregation pass also writes the tables out
@@ -34,8 +35,15 @@ struct PassArgs {
   int32_t *dirty_list;       // [n] those vertices, sc->tab_dirty of them
   int2 *upd_list;            // chunks {mover, chunk} of the movers' rows, listed by the
                              // apply step when tables are kept (else nullptr)
-  int32_t *movers;           // movers of degree <= 4096, listed by the apply step of a
+  int32_t *movers;           // movers that are not hubs, listed by the apply step of a
                              // call's last pass (one graph; else nullptr), sc->n_movers
+  int64_t hub_min;           // rows longer than this are hubs (BinPlan::hub_min)
+  // afterburner: candidate bitmap (bit v of word v / 32) and the candidates
+  // of each group, listed by the record pass into ab_list[ab_off[g] ...)
+  uint32_t *inL;
+  int32_t *ab_list;
+  int64_t ab_off[kAbGroups];  // start of group g (the offset of its first bin)
+  int64_t ab_max[kAbGroups];  // largest degree in group g (BinPlan)
 };
 
 // Vertex lists of the degree bins of one level (stable: ascending ids).
@@ -60,14 +68,18 @@ inline BinRange bin_range(const Bins &b, int lo, int hi) {
 void configure_kernels();
 // Builds b.lists / b.offs on the stream; the caller copies b.offs to the host
 // and fills b.list / b.count (see finish_bins).
-void build_bins(const LevelGraph &g, Bins &b, int32_t *scan_tmp, cudaStream_t s);
+void build_bins(const LevelGraph &g, const BinPlan &plan, Bins &b, int32_t *scan_tmp, cudaStream_t s);
 void finish_bins(Bins &b, const int32_t *h_offs);
 
 // Launchers return the number of kernels they launched.
 void launch_hub_rows(const int64_t *rp, const int32_t *vtx, int H, int64_t *out, cudaStream_t s);
-void launch_pass_begin(Scalars *sc, cudaStream_t s);
+// Resets the pass counters; advance = 1 also loads the pass's temperature
+// from the device schedule (sc->phi_tab) and moves to the next pass.
+void launch_pass_begin(Scalars *sc, cudaStream_t s, int advance = 0);
 int launch_first_pass(const PassArgs &a, const Bins &b, cudaStream_t s);
 int launch_move(const PassArgs &a, const Bins &b, cudaStream_t s);
+// Fills the afterburner groups' list offsets and degree bounds of a level.
+void set_ab_groups(PassArgs &a, const Bins &b, const BinPlan &plan);
 int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
 // Ablations of the afterburner: every candidate moves, or (mlh) all but a
 // vertex alone in its cluster whose destination is another one-vertex

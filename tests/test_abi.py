@@ -62,7 +62,7 @@ def test_struct_layouts_match_c(tmp_path):
         " sizeof(lc_result), sizeof(lc_event), sizeof(lc_csr), offsetof(lc_opts, stream),"
         " offsetof(lc_result, error_detail), sizeof(lc_server_config), offsetof(lc_server_config, opts),"
         " offsetof(lc_opts, tables), offsetof(lc_result, kernel_bytes), offsetof(lc_result, tables_rebuilt),"
-        " offsetof(lc_opts, alloc), offsetof(lc_opts, alloc_ctx), offsetof(lc_result, scratch_peak_bytes),"
+        " offsetof(lc_opts, alloc), offsetof(lc_opts, graphs), offsetof(lc_result, scratch_peak_bytes),"
         " (int)LC_K_COUNT);"
         "return 0;}\n")
     exe = tmp_path / "sizes"
@@ -72,7 +72,7 @@ def test_struct_layouts_match_c(tmp_path):
                     ctypes.sizeof(lc._Csr), lc._Opts.stream.offset, lc._Result.error_detail.offset,
                     ctypes.sizeof(lc._ServerConfig), lc._ServerConfig.opts.offset, lc._Opts.tables.offset,
                     lc._Result.kernel_bytes.offset, lc._Result.tables_rebuilt.offset,
-                    lc._Opts.alloc.offset, lc._Opts.alloc_ctx.offset, lc._Result.scratch_peak_bytes.offset,
+                    lc._Opts.alloc.offset, lc._Opts.graphs.offset, lc._Result.scratch_peak_bytes.offset,
                     len(lc.LC_K_NAMES)]
 
 

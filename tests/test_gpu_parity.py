@@ -330,3 +330,69 @@ def test_validation_errors():
     big = vw.copy()
     big[:] = 1 << 40
     assert run(rp, col, ew, big, lam=(1, 1)) == 6
+
+
+BIN_PLANS = [
+    dict(),  # defaults
+    dict(bins=(8, 16, 32, 128, 256, 256, 256, 256, 256)),  # every row above 256 is a hub
+    dict(bins=(4, 16, 32, 64, 256, 512, 1024, 2048, 2048), hub_chunk=1024),  # no bin 8
+    dict(bins=(8, 8, 8, 128, 128, 512, 512, 2048, 4096), hub_chunk=4096),  # empty lane bins
+    dict(bins=(2, 3, 20, 100, 200, 300, 700, 1500, 3000), hub_chunk=256),
+]
+
+
+@pytest.mark.parametrize("plan", range(len(BIN_PLANS)))
+def test_bin_plans_give_identical_results(plan):
+    """The degree bins and hub chunks only decide which kernel handles a
+    vertex (Section IV-C-2 leaves them open); every plan must give the
+    oracle's labels, passes and objective."""
+    for g in (gg.rmat(15, seed=3), gg.sbm_planted(n=4000, blocks=40, p_in=0.06, p_out=0.002, seed=4),
+              gg.grid_cpm(side=16)):
+        labels, res, ev = gpu_cluster(g, opts=lc.Options(**BIN_PLANS[plan]), trace=True)
+        ref, ores, oev = oracle.louvain_plus(g, trace=True, trace_passes=True)
+        assert np.array_equal(labels, ref), g.name
+        assert res["phi"] == ores["phi"] and res["passes_total"] == ores["passes_total"], g.name
+        compare_traces(ev, oev)
+
+
+def test_invalid_bin_plans_rejected():
+    g = gg.rmat(9, seed=1)
+    for kw in (dict(bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 5000)),  # above bin 8's capacity
+               dict(bins=(8, 16, 32, 128, 100)),  # decreasing
+               dict(hub_chunk=100), dict(hub_chunk=1 << 20),
+               dict(tables=1, bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 2048))):
+        with pytest.raises(lc.LCError) as e:
+            gpu_cluster(g, opts=lc.Options(**kw))
+        assert e.value.code == 1, kw  # LC_ERR_ARG
+
+
+@pytest.mark.parametrize("plan", [0, 2])
+def test_graph_replay_gives_identical_results(plan):
+    """opts.graphs replays the repeated passes of each LocalMovePasses call
+    from one captured CUDA graph (temperature read from the device): labels,
+    objective and pass counts equal the oracle's, alone and in a batch."""
+    graphs = [gg.rmat(14, seed=7), gg.sbm_planted(n=3000, blocks=30, p_in=0.05, p_out=0.002, seed=8),
+              gg.grid_cpm(side=14), gg.rmat(8, seed=9)]
+    opts = lc.Options(graphs=True, **BIN_PLANS[plan])
+    for g in graphs:
+        for uncoarsen in (True, False):
+            o = lc.Options(graphs=True, uncoarsen=uncoarsen, **BIN_PLANS[plan])
+            labels, res, _ = gpu_cluster(g, opts=o)
+            ref, ores, _ = oracle.louvain_plus(g, oracle.Params(uncoarsen=uncoarsen))
+            assert np.array_equal(labels, ref), (g.name, uncoarsen)
+            assert res["phi"] == ores["phi"] and res["passes_total"] == ores["passes_total"], g.name
+    pack = gg.pack(graphs)
+    labels, res = lc.lc_cluster_batch(dev(pack["row_ptr"]), dev(pack["col"]), dev(pack["ew"]), dev(pack["vw"]),
+                                      pack["graph_ptr"], pack["lam_num"], pack["lam_den"], opts=opts)
+    labels = labels.cpu().numpy()
+    gp = pack["graph_ptr"]
+    for k, g in enumerate(graphs):
+        ref, ores, _ = oracle.louvain_plus(g)
+        assert np.array_equal(labels[gp[k]:gp[k + 1]], ref), g.name
+        assert res[k]["phi"] == ores["phi"], g.name
+    # on the legacy default stream too (the capture runs on a library stream)
+    g = graphs[0]
+    labels, res = lc.lc_cluster(dev(g.row_ptr), dev(g.col), dev(g.ew), dev(g.vw), g.lam_num, g.lam_den,
+                                opts=opts, stream=torch.cuda.default_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(labels.cpu().numpy(), oracle.louvain_plus(g)[0])

@@ -167,6 +167,10 @@ typedef struct {
                                not depend on them; lc_autotune picks them by timing.
                                opts.tables = 1 needs the defaults. */
   int32_t hub_chunk;        /* edges per hub chunk; 0 = 2048; 256 .. 65536 */
+  int32_t ab_threads[5];    /* threads per candidate in the afterburner's launch groups
+                               (bin 0, bin 1, bins 2-4, bins 5-6, bins 7-8): 0 = the
+                               default (1, 16, 32, 128, 512); groups 2-4 also take 32, 128
+                               or 512.  Results do not depend on them. */
   int32_t graphs;           /* 1 = the passes of a LocalMovePasses call that repeat the same
                                launches (all but a first pass from singletons and the last)
                                are captured once per call into a CUDA graph and replayed,
@@ -230,13 +234,15 @@ LC_API int64_t lc_scratch_estimate(int64_t n, int64_t nnz, int32_t count, const 
 typedef struct {
   int32_t bin_max_deg[9]; /* for lc_opts.bin_max_deg */
   int32_t hub_chunk;      /* for lc_opts.hub_chunk */
+  int32_t ab_threads[5];  /* for lc_opts.ab_threads */
   int32_t graphs;         /* for lc_opts.graphs */
   int32_t trials;         /* settings timed */
   double ms_default;      /* median milliseconds of one call with the starting settings */
   double ms_best;         /* ... with the chosen ones */
 } lc_tuning;
 
-/* Picks the degree-bin boundaries, hub chunk length and graph replay for a
+/* Picks the degree-bin boundaries, hub chunk length, afterburner thread
+ * groups and graph replay for a
  * workload by timing them (the paper leaves its bucket thresholds open,
  * Section IV-C-2; no setting changes a result).  Starting from opts (NULL:
  * the defaults), it moves one setting at a time, runs lc_cluster (count = 1)

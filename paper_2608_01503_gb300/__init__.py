@@ -103,7 +103,8 @@ class _Opts(ctypes.Structure):
                 ("symmetry", ctypes.c_int32), ("tables", ctypes.c_int32),
                 ("scratch_limit", ctypes.c_int64), ("alloc", _AllocFn), ("dealloc", _FreeFn),
                 ("alloc_ctx", ctypes.c_void_p), ("bin_max_deg", ctypes.c_int32 * 9),
-                ("hub_chunk", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("hub_chunk", ctypes.c_int32), ("ab_threads", ctypes.c_int32 * 5),
+                ("graphs", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
@@ -119,7 +120,7 @@ class _Result(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("bin_max_deg", ctypes.c_int32 * 9), ("hub_chunk", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("ab_threads", ctypes.c_int32 * 5), ("graphs", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double)]
 
 
@@ -219,6 +220,7 @@ class Options:
     bins: tuple = ()  # upper degrees of the 9 shared-memory bins (0 or missing = default)
     hub_chunk: int = 0  # edges per hub chunk (0 = default)
     graphs: bool = False  # replay the repeated passes of each LocalMovePasses call from a CUDA graph
+    ab_threads: tuple = ()  # threads per candidate of the 5 afterburner groups (0 = default)
 
 
 def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
@@ -245,6 +247,11 @@ def _c_opts(o: Options | None, stream, event_fn=None) -> _Opts:
     for k in range(9):
         c.bin_max_deg[k] = int(bins[k])
     c.hub_chunk = int(o.hub_chunk)
+    abt = list(o.ab_threads) + [0] * (5 - len(o.ab_threads))
+    if len(abt) != 5:
+        raise ValueError("ab_threads holds at most 5 entries")
+    for k in range(5):
+        c.ab_threads[k] = int(abt[k])
     c.graphs = int(bool(o.graphs))
     c.stream = stream
     if event_fn is not None:
@@ -548,7 +555,8 @@ def lc_autotune(row_ptr, col, ew, vw, lambda_num, lambda_den, graph_ptr=None,
                          gp.ctypes.data if gp is not None else None, ln.ctypes.data, ld.ctypes.data,
                          ctypes.byref(c), int(repeats), ctypes.byref(t))
     _check(rc)
-    return {"bins": list(t.bin_max_deg), "hub_chunk": t.hub_chunk, "graphs": bool(t.graphs),
+    return {"bins": list(t.bin_max_deg), "hub_chunk": t.hub_chunk, "ab_threads": list(t.ab_threads),
+            "graphs": bool(t.graphs),
             "trials": t.trials, "ms_default": t.ms_default, "ms_best": t.ms_best}
 
 
@@ -557,6 +565,7 @@ def tuned_options(tuning: dict | None, **kw) -> Options:
     if tuning:
         kw.setdefault("bins", tuple(tuning["bins"]))
         kw.setdefault("hub_chunk", int(tuning["hub_chunk"]))
+        kw.setdefault("ab_threads", tuple(tuning.get("ab_threads", ())))
         kw.setdefault("graphs", bool(tuning["graphs"]))
     return Options(**kw)
 

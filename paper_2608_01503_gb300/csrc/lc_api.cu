@@ -270,6 +270,13 @@ static int resolve_plan(const lc_opts &o, BinPlan *out) {
     if (o.hub_chunk < 256 || o.hub_chunk > 65536) return LC_ERR_ARG;
     p.hub_chunk = o.hub_chunk;
   }
+  for (int g = 0; g < 5; ++g) {
+    const int32_t t = o.ab_threads[g];
+    if (t == 0) continue;
+    const bool fixed = g < 2 && t == p.ab_gs[g];  // bins 0 and 1 have one layout each
+    if (!fixed && !(g >= 2 && (t == 32 || t == 128 || t == 512))) return LC_ERR_ARG;
+    p.ab_gs[g] = t;
+  }
   // kept tables share the shared-memory layout of the default bins (tab_cap)
   if (o.tables == 1 && !is_default_plan(p)) return LC_ERR_ARG;
   *out = p;
@@ -590,6 +597,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
         a.tab_build = tables && i < r.o.pass_limit;
         r.prof.begin(LC_K_MOVE);
         r.res->kernel_launches[LC_K_MOVE] += launch_move(a, L.bins, r.s);
+        // + 8 B per distinct adjacent cluster (its W(X)), added from sc->distinct_x at the end
         r.prof.end(12.0 * nnz + 48.0 * n + (a.tab_build ? 16.0 * nnz : 0.0));
         kept = a.tab_build != 0;
         a.tab_build = 0;
@@ -1069,6 +1077,11 @@ static void end_call(Run &r, int rc) {
         cudaMemcpyAsync(&upd, &r.sc->tab_upd_edges, sizeof(upd), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
         cudaStreamSynchronize(r.s) == cudaSuccess)
       r.res->kernel_bytes[LC_K_TABLE] += 40.0 * (double)upd;
+    long long nx = 0;  // move step: W(X) of each distinct adjacent cluster of each vertex
+    if (r.sc &&
+        cudaMemcpyAsync(&nx, &r.sc->distinct_x, sizeof(nx), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&
+        cudaStreamSynchronize(r.s) == cudaSuccess)
+      r.res->kernel_bytes[LC_K_MOVE] += 8.0 * (double)nx;
     long long dph = 0;  // final objective: col, ew, C[u], M[u] of each mover edge
     if (r.sc &&
         cudaMemcpyAsync(&dph, &r.sc->dphi_edges, sizeof(dph), cudaMemcpyDeviceToHost, r.s) == cudaSuccess &&

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
 __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const int32_t *__restrict__ list,
                                                         int64_t count) {
   constexpr int K = 8;
-  long long cntL = 0, phi = 0;
+  long long cntL = 0, phi = 0, nX = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = list[i];
@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const int32_
         }
       }
       if (first) {
+        nX++;
         const long long g = gain_other(P, S, wv, WX[j]);
         if (better(g, X[j], gb, xb)) {
           gb = g;
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const int32_
     add_self(a, v, gC, phi);
     decide(a, P, v, gC, xb, gb, cntL);
   }
+  flush_block_sum(nX, &a.sc->distinct_x);
   flush_block_sum(cntL, &a.sc->count_L);
   flush_block_sum(phi, &a.phi_acc[0]);
 }
@@ -192,7 +194,7 @@ template <int G>
 __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *__restrict__ list,
                                                     int64_t count) {
   __shared__ int32_t acc[256];
-  long long cntL = 0, phi = 0;
+  long long cntL = 0, phi = 0, nX = 0;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
   const int wbase = threadIdx.x & ~31;
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
     if (other && lane == leader) {
       g = gain_other(P, acc[threadIdx.x], wv, WX);
       x = X;
+      nX++;
     }
     group_argmax<G>(g, x);
     if (active && sub == 0) {
@@ -236,6 +239,7 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
     }
     __syncwarp();
   });
+  flush_block_sum(nX, &a.sc->distinct_x);
   flush_block_sum(cntL, &a.sc->count_L);
   flush_block_sum(phi, &a.phi_acc[0]);
 }
@@ -257,7 +261,7 @@ template <int GS>
 __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam &P,
                                              unsigned long long *tab, uint32_t s0, uint32_t s1,
                                              long long wv, int r, long long &gb, int32_t &xb,
-                                             bool keep = false) {
+                                             long long &nX, bool keep = false) {
   constexpr int U = 4;
   const long long Lam = P.Lam, muw = P.mu * wv;
   for (uint32_t base = s0 + r; base < s1; base += GS * U) {
@@ -274,6 +278,7 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (t[k] == kEmptySlot) continue;
+      nX++;
       const int32_t X = slot_key(t[k]);
       const long long g = Lam * (long long)slot_val(t[k]) - muw * WX[k];
       if (better(g, X, gb, xb)) {
@@ -380,7 +385,7 @@ __device__ __forceinline__ long long split_insert_row(const PassArgs &a, int64_t
 template <int GS, bool BUILD>
 __device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam &P, SplitTab t,
                                              uint32_t cap, long long wv, int r, long long &gb,
-                                             int32_t &xb, unsigned long long *gt) {
+                                             int32_t &xb, unsigned long long *gt, long long &nX) {
   constexpr int U = 4;
   const long long Lam = P.Lam, muw = P.mu * wv;
   for (uint32_t base = r; base < cap; base += GS * U) {
@@ -410,6 +415,7 @@ __device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (key[k] == 0u) continue;
+      nX++;
       const int32_t X = (int32_t)(key[k] - 1u);
       const long long g = Lam * (long long)S[k] - muw * WX[k];
       if (better(g, X, gb, xb)) {
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
   constexpr int U = SLOTS / 128;  // edges per lane per batch: 64 (bin 3) or 128 (bin 4)
   __shared__ uint32_t keys[kWarpBinWarps][SLOTS];
   __shared__ int32_t vals[kWarpBinWarps][SLOTS];
-  long long cntL = 0, phi = 0;
+  long long cntL = 0, phi = 0, nX = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SplitTab tab{keys[wid], vals[wid]};
   for (int s = lane; s < SLOTS; s += 32) {
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
     __syncwarp();
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
-    split_argmax<32, false>(a, P, tab, cap, wv, lane, gb, xb, nullptr);
+    split_argmax<32, false>(a, P, tab, cap, wv, lane, gb, xb, nullptr, nX);
     group_argmax<32>(gb, xb);
     self = warp_sum(self);
     if (lane == 0) {
@@ -461,6 +467,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
     }
     __syncwarp();
   });
+  flush_block_sum(nX, &a.sc->distinct_x);
   flush_block_sum(cntL, &a.sc->count_L);
   flush_block_sum(phi, &a.phi_acc[0]);
 }
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
   __shared__ long long rg[2][GS / 32];
   __shared__ int32_t rx[2][GS / 32];
   int par = 0;
-  long long cntL = 0, phi = 0;
+  long long cntL = 0, phi = 0, nX = 0;
   for (int s = threadIdx.x; s < SLOTS; s += GS) {
     tab.key[s] = 0u;
     tab.val[s] = 0;
@@ -504,7 +511,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
     unsigned long long *gt = a.gtab + 2 * beg;
-    split_argmax<GS, BUILD>(a, P, tab, cap, wv, threadIdx.x, gb, xb, gt);
+    split_argmax<GS, BUILD>(a, P, tab, cap, wv, threadIdx.x, gb, xb, gt, nX);
     // one reduction of (best gain, cluster, S_self) for thread 0 only: warp
     // level, one barrier, thread 0 combines the warps
     group_argmax<32>(gb, xb);
@@ -533,6 +540,7 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
     }
     par ^= 1;
   }
+  flush_block_sum(nX, &a.sc->distinct_x);
   flush_block_sum(cntL, &a.sc->count_L);
   flush_block_sum(phi, &a.phi_acc[0]);
 }
@@ -558,10 +566,12 @@ __device__ __forceinline__ void hub_acc_add(const PassArgs &a, int h, long long 
 
 // Move, step 1: insert a chunk of a hub row into the hub's global table.
 // Lanes of a warp holding the same cluster are combined first
-// (__match_any_sync), so a popular cluster costs one global atomic per warp.
+// (__match_any_sync), so a popular cluster costs one global atomic per warp;
+// the U edges a lane holds are matched together and their leaders' inserts
+// go out as one batch (table_add_batch), so the atomics overlap.
 __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
   constexpr int U = 4;
-  __shared__ int32_t acc[kHubThreads];
+  __shared__ int32_t acc[U][kHubThreads];
   const int c = blockIdx.x;
   const int h = a.hub.hub_of[c];
   const int32_t v = a.hub.vtx[h];
@@ -587,24 +597,31 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
+    bool other[U];
+    int leader[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-      const bool other = u[k] >= 0 && X[k] != Cv;
+      other[k] = u[k] >= 0 && X[k] != Cv;
       if (u[k] >= 0 && X[k] == Cv) self += w[k];
       const unsigned long long key =
-          other ? (unsigned long long)(uint32_t)X[k] : (0xFFFFFFFF00000000ull | lane);
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-      const int leader = __ffs(peers) - 1;
-      acc[threadIdx.x] = 0;
-      __syncwarp();
-      if (other) atomicAdd(&acc[wbase + leader], w[k]);
-      __syncwarp();
-      if (other && lane == leader) {
-        bool fresh = false;
-        ok &= table_add(tab, cap, X[k], acc[threadIdx.x], fresh);
-      }
-      __syncwarp();
+          other[k] ? (unsigned long long)(uint32_t)X[k] : (0xFFFFFFFF00000000ull | lane);
+      leader[k] = __ffs(__match_any_sync(0xFFFFFFFFu, key)) - 1;
+      acc[k][threadIdx.x] = 0;
     }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (other[k]) atomicAdd(&acc[k][wbase + leader[k]], w[k]);
+    __syncwarp();
+    bool lead[U];
+    int32_t sum[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      lead[k] = other[k] && lane == leader[k];
+      sum[k] = lead[k] ? acc[k][threadIdx.x] : 0;
+    }
+    __syncwarp();  // acc is cleared again by the next batch
+    table_add_batch<U>(tab, cap, X, sum, lead, ok);
   }
   if (!ok) a.sc->error = 1;
   hub_acc_add(a, h, self);
@@ -619,12 +636,13 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_scan(PassArgs a) {
   const int64_t beg = a.g.rp[v];
   const long long wv = a.g.vw[v];
   const GraphParam P = a.gp[graph_of(a, v)];
-  long long gb = LLONG_MIN;
+  long long gb = LLONG_MIN, nX = 0;
   int32_t xb = kNone;
   range_argmax<kHubThreads>(a, P, a.gtab + 2 * beg, (uint32_t)(2 * (a.hub.e0[c] - beg)),
-                            (uint32_t)(2 * (a.hub.e1[c] - beg)), wv, threadIdx.x, gb, xb,
+                            (uint32_t)(2 * (a.hub.e1[c] - beg)), wv, threadIdx.x, gb, xb, nX,
                             a.tab_build != 0);
   hub_part_store(a, c, gb, xb);
+  flush_block_sum(nX, &a.sc->distinct_x);
 }
 
 // First pass: argmax over a chunk of a hub row.
@@ -1572,7 +1590,15 @@ void set_ab_groups(PassArgs &a, const Bins &b, const BinPlan &plan) {
   for (int g = 0; g < kAbGroups; ++g) {
     a.ab_off[g] = b.list[kAbFirstBin[g]] - b.list[0];
     a.ab_max[g] = plan.max_deg[kAbFirstBin[g + 1] - 1];
+    a.ab_gs[g] = plan.ab_gs[g];
   }
+}
+
+// Groups 2-4: 32, 128 or 512 threads per candidate (BinPlan::ab_gs).
+static int launch_ab_wide_group(const PassArgs &a, const Bins &b, int g, cudaStream_t s) {
+  if (a.ab_gs[g] == 32) return launch_ab_group<32>(a, b, g, s);
+  if (a.ab_gs[g] == 128) return launch_ab_group<128>(a, b, g, s);
+  return launch_ab_group<512>(a, b, g, s);
 }
 
 int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s) {
@@ -1580,9 +1606,7 @@ int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s) {
   k_ab_prep<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
   n += launch_ab_group<1>(a, b, 0, s);
   n += launch_ab_group<16>(a, b, 1, s);
-  n += launch_ab_group<32>(a, b, 2, s);
-  n += launch_ab_group<128>(a, b, 3, s);
-  n += launch_ab_group<512>(a, b, 4, s);
+  for (int g = 2; g < kAbGroups; ++g) n += launch_ab_wide_group(a, b, g, s);
   if (a.hub.H > 0) {
     k_hub_afterburner<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     k_hub_ab_final<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a);

@@ -44,6 +44,7 @@ struct PassArgs {
   int32_t *ab_list;
   int64_t ab_off[kAbGroups];  // start of group g (the offset of its first bin)
   int64_t ab_max[kAbGroups];  // largest degree in group g (BinPlan)
+  int32_t ab_gs[kAbGroups];   // threads per candidate in group g (BinPlan)
 };
 
 // Vertex lists of the degree bins of one level (stable: ascending ids).

@@ -71,6 +71,7 @@ int time_setting(const Workload &w, const lc_opts &o, int repeats, double *ms,
 }
 
 const int kDefaultMax[9] = {8, 16, 32, 128, 256, 512, 1024, 2048, 4096};
+const int kDefaultAb[5] = {1, 16, 32, 128, 512};
 
 }  // namespace
 
@@ -145,7 +146,17 @@ extern "C" LC_API int lc_autotune(const lc_csr *g, const int64_t *vertex_w, cons
     c.bin_max_deg[k] = v;
     rc = try_setting(c);
   }
-  // 4. CUDA-graph replay of the repeated passes
+  // 4. threads per candidate in the afterburner's wide groups
+  for (int g : {3, 4}) {
+    for (int t : {32, 128, 512}) {
+      if (rc != LC_OK) break;
+      lc_opts c = cur;
+      if ((c.ab_threads[g] ? c.ab_threads[g] : kDefaultAb[g]) == t) continue;
+      c.ab_threads[g] = t;
+      rc = try_setting(c);
+    }
+  }
+  // 5. CUDA-graph replay of the repeated passes
   if (rc == LC_OK) {
     lc_opts c = cur;
     c.graphs = 1;
@@ -155,6 +166,7 @@ extern "C" LC_API int lc_autotune(const lc_csr *g, const int64_t *vertex_w, cons
   if (cudaStreamSynchronize(s) != cudaSuccess && rc == LC_OK) rc = LC_ERR_CUDA;
   if (rc != LC_OK) return rc;
   for (int k = 0; k < 9; ++k) out->bin_max_deg[k] = cur.bin_max_deg[k];
+  for (int k = 0; k < 5; ++k) out->ab_threads[k] = cur.ab_threads[k] ? cur.ab_threads[k] : kDefaultAb[k];
   out->hub_chunk = cur.hub_chunk;
   out->graphs = cur.graphs;
   out->ms_best = best;

@@ -676,12 +676,23 @@ def main():
     rp, col, ew, vw = t(g.row_ptr), t(g.col), t(g.ew), t(g.vw)
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts_prof = lc.Options(profile=True, tables=args.tables)
+    # launch settings: lc_autotune's choice for this workload and GPU when
+    # cached (--tune makes one), else the defaults; results are identical
+    key = _gpu_key(args.workload if args.scale is None else f"{args.workload}_s{args.scale}")
+    tuning = None
+    if args.tables == 0 and not args.no_tuning:
+        tuning = lc.load_tuning(key)
+        if args.tune:
+            tuning = lc.lc_autotune(rp, col, ew, vw, g.lam_num, g.lam_den, repeats=3)
+            if rank == 0:
+                lc.save_tuning(key, tuning)
+    opts_prof = lc.tuned_options(tuning, profile=True, tables=args.tables)
 
     K = max(1, args.iterations)
 
     if args.method != "louvain+":  # pLeiden (no uncoarsening) or pLeiden+
-        opts_prof = lc.Options(profile=True, uncoarsen=args.method == "leiden+", tables=args.tables)
+        opts_prof = lc.tuned_options(tuning, profile=True, uncoarsen=args.method == "leiden+",
+                                     tables=args.tables)
 
     def call():
         if args.method != "louvain+":
@@ -733,16 +744,15 @@ def main():
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         h_rp, h_col, h_ew, h_vw = pin(g.row_ptr), pin(g.col), pin(g.ew), pin(g.vw)
         h_lab = torch.empty(g.n, dtype=torch.int32).pin_memory().numpy()
-        lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab,
-                               opts=lc.Options(tables=args.tables))
+        opts_e2e = lc.tuned_options(tuning, tables=args.tables)
+        lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab, opts=opts_e2e)
         k2 = max(1, min(args.steps, 5))
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(k2):
-            lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab,
-                               opts=lc.Options(tables=args.tables))
+            lc.lc_cluster_host(h_rp, h_col, h_ew, h_vw, g.lam_num, g.lam_den, labels_out=h_lab, opts=opts_e2e)
         torch.cuda.synchronize(dev)
         e2e_s = (time.perf_counter() - t0) / k2
         if dist:
@@ -782,6 +792,7 @@ def main():
                    "n": g.n, "nnz": g.nnz, "edges_counted": "nnz = 2m (both directions), the paper's 2m/t",
                    "l2": "inputs larger than L2 (CSR > 129 MB); no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU", "method": args.method,
+                   "settings": "tuned" if tuning else "default", "tuning": tuning,
                    **({"iterations": K, "edges_counted_iterated": "nnz once per iteration"}
                       if K > 1 else {})},
         "result": {"n_clusters": res["n_clusters"], "levels": res["levels"],

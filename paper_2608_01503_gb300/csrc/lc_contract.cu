@@ -125,10 +125,13 @@ __device__ __forceinline__ int insert_edges(const InsertArgs &a, int32_t x, int6
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) y[k] = u[k] >= 0 ? a.Cd[u[k]] : x;
-    bool todo[U];
 #pragma unroll
-    for (int k = 0; k < U; ++k) todo[k] = y[k] != x;
-    fresh_n += table_add_batch<U>(tab, cap, y, w, todo, ok);
+    for (int k = 0; k < U; ++k) {
+      if (y[k] == x) continue;
+      bool fresh = false;
+      ok &= table_add(tab, cap, y[k], w[k], fresh);
+      fresh_n += fresh;
+    }
   }
   return fresh_n;
 }

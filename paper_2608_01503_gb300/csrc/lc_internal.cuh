@@ -199,10 +199,9 @@ __device__ __forceinline__ int32_t slot_val(unsigned long long s) { return (int3
 // violation (every caller sizes tables to at least twice its distinct keys).
 // When this call claimed a new slot, `fresh` is set and `slot` names it.
 __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap, int32_t key,
-                                          int32_t w, bool &fresh, uint32_t &slot,
-                                          uint32_t start = 0xFFFFFFFFu) {
+                                          int32_t w, bool &fresh, uint32_t &slot) {
   const unsigned long long tag = (unsigned long long)((uint32_t)key + 1u) << 32;
-  uint32_t s = start == 0xFFFFFFFFu ? slot_of(key, cap) : start;
+  uint32_t s = slot_of(key, cap);
   for (uint32_t probe = 0; probe < cap; ++probe) {
     unsigned long long cur = tab[s];
     if (cur == kEmptySlot) {
@@ -228,56 +227,6 @@ __device__ __forceinline__ bool table_add(unsigned long long *tab, uint32_t cap,
                                           int32_t w, bool &fresh) {
   uint32_t slot;
   return table_add(tab, cap, key, w, fresh, slot);
-}
-
-// table_add for U entries at once (those with todo[k]), so that their
-// memory operations overlap instead of waiting on each other: the first
-// probe of every entry is read, then every empty one is claimed by CAS, then
-// every entry whose slot holds its key adds its weight; only entries that
-// met another key probe on, one by one.  Returns how many slots this call
-// claimed; ok turns false on a bound violation (as table_add).
-template <int U>
-__device__ __forceinline__ int table_add_batch(unsigned long long *tab, uint32_t cap, const int32_t (&key)[U],
-                                               const int32_t (&w)[U], const bool (&todo)[U], bool &ok) {
-  uint32_t sl[U];
-  unsigned long long cur[U];
-  bool done[U];
-  int fresh_n = 0;
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    sl[k] = todo[k] ? slot_of(key[k], cap) : 0u;
-    cur[k] = todo[k] ? tab[sl[k]] : 0ull;
-    done[k] = !todo[k];
-  }
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    if (done[k] || cur[k] != kEmptySlot) continue;
-    const unsigned long long tag = (unsigned long long)((uint32_t)key[k] + 1u) << 32;
-    cur[k] = atomicCAS(&tab[sl[k]], kEmptySlot, tag | (uint32_t)w[k]);
-    if (cur[k] == kEmptySlot) {
-      done[k] = true;
-      fresh_n++;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    if (done[k]) continue;
-    const unsigned long long tag = (unsigned long long)((uint32_t)key[k] + 1u) << 32;
-    if ((cur[k] & 0xFFFFFFFF00000000ull) == tag) {
-      atomicAdd(reinterpret_cast<unsigned int *>(&tab[sl[k]]), (unsigned int)w[k]);
-      done[k] = true;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    if (done[k]) continue;
-    bool fresh = false;
-    uint32_t slot;
-    // probing on from the next slot: the first one held another key
-    ok &= table_add(tab, cap, key[k], w[k], fresh, slot, sl[k] + 1 == cap ? 0u : sl[k] + 1);
-    fresh_n += fresh;
-  }
-  return fresh_n;
 }
 
 // --------------------------------------------------------------- gains

@@ -566,12 +566,10 @@ __device__ __forceinline__ void hub_acc_add(const PassArgs &a, int h, long long 
 
 // Move, step 1: insert a chunk of a hub row into the hub's global table.
 // Lanes of a warp holding the same cluster are combined first
-// (__match_any_sync), so a popular cluster costs one global atomic per warp;
-// the U edges a lane holds are matched together and their leaders' inserts
-// go out as one batch (table_add_batch), so the atomics overlap.
+// (__match_any_sync), so a popular cluster costs one global atomic per warp.
 __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
   constexpr int U = 4;
-  __shared__ int32_t acc[U][kHubThreads];
+  __shared__ int32_t acc[kHubThreads];
   const int c = blockIdx.x;
   const int h = a.hub.hub_of[c];
   const int32_t v = a.hub.vtx[h];
@@ -597,31 +595,24 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
-    bool other[U];
-    int leader[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-      other[k] = u[k] >= 0 && X[k] != Cv;
+      const bool other = u[k] >= 0 && X[k] != Cv;
       if (u[k] >= 0 && X[k] == Cv) self += w[k];
       const unsigned long long key =
-          other[k] ? (unsigned long long)(uint32_t)X[k] : (0xFFFFFFFF00000000ull | lane);
-      leader[k] = __ffs(__match_any_sync(0xFFFFFFFFu, key)) - 1;
-      acc[k][threadIdx.x] = 0;
+          other ? (unsigned long long)(uint32_t)X[k] : (0xFFFFFFFF00000000ull | lane);
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+      const int leader = __ffs(peers) - 1;
+      acc[threadIdx.x] = 0;
+      __syncwarp();
+      if (other) atomicAdd(&acc[wbase + leader], w[k]);
+      __syncwarp();
+      if (other && lane == leader) {
+        bool fresh = false;
+        ok &= table_add(tab, cap, X[k], acc[threadIdx.x], fresh);
+      }
+      __syncwarp();
     }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < U; ++k)
-      if (other[k]) atomicAdd(&acc[k][wbase + leader[k]], w[k]);
-    __syncwarp();
-    bool lead[U];
-    int32_t sum[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      lead[k] = other[k] && lane == leader[k];
-      sum[k] = lead[k] ? acc[k][threadIdx.x] : 0;
-    }
-    __syncwarp();  // acc is cleared again by the next batch
-    table_add_batch<U>(tab, cap, X, sum, lead, ok);
   }
   if (!ok) a.sc->error = 1;
   hub_acc_add(a, h, self);

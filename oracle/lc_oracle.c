@@ -1047,11 +1047,9 @@ static int pleiden_refine(const orc_graph *g, const orc_params *p, const int32_t
     H[v] = v;
     if (!inU[v]) continue;
     /* ChooseRandom: the candidate c (v itself or a qualifying neighbour)
-     * with the smallest (rand(v, c), c), independent of the order of the
-     * row; v's own draw is moved into the top 2^-16 of the range, so v
-     * keeps no edge with probability at most 2^-16 when a neighbour
-     * qualifies (non-zero, as Lemma 2 needs) and always when none does. */
-    uint64_t best = (orc_rand(p->seed, level, 0, (v << 32) | v) >> 16) | (0xFFFFull << 48);
+     * with the smallest (rand(v, c), c); uniform over the candidates and
+     * independent of the order of the row. */
+    uint64_t best = orc_rand(p->seed, level, 0, (v << 32) | v);
     for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
       const int64_t u = g->col[e];
       if (inU[u] && B[u] == B[v] &&

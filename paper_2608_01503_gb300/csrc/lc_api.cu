@@ -153,7 +153,7 @@ struct Run {
   uint8_t *M = nullptr, *E = nullptr;
   AbRec *ab = nullptr;
   uint32_t *inL = nullptr;    // afterburner candidate bitmap
-  int32_t *ab_list = nullptr; // afterburner candidates by group
+  AbWork *ab_list = nullptr;  // afterburner candidates by group, with their work records
   int2 *upd_list = nullptr;
   unsigned long long *gtab = nullptr;
   long long *gself = nullptr;
@@ -294,7 +294,7 @@ static int64_t level0_scratch_bytes(int64_t n0, int64_t nnz0, int64_t G, int tab
   if (tables == 1) b += 2 * 4 * n + 8 * upd_list_size(n0, nnz0);
   b += 4 * scan_scratch(big);                                // scan32
   b += 2 * 8 * n + (int64_t)sizeof(AbRec) * n;               // W, delta, ab
-  b += 4 * ((n0 + 31) / 32 + 1) + 4 * n;                     // inL, ab_list
+  b += 4 * ((n0 + 31) / 32 + 1) + (int64_t)sizeof(AbWork) * n;  // inL, ab_list
   b += 2 * 8 * (n0 + 1) + 8 * scan_scratch(n0 + 1) + 2 * n;  // bound, off, scan64, M, E
   b += 8 * (2 * nnz0 > 0 ? 2 * nnz0 : 1);                    // gtab
   if (G > 1) b += 8 * n + 8 * (G + 1) + 4 * n;               // gself, graph_ptr, gid

@@ -129,6 +129,18 @@ struct __align__(16) AbRec {
   long long q;
 };
 
+// Everything the afterburner needs about one listed candidate v itself, written
+// by the record pass beside its list entry so that the group kernels read it
+// in one coalesced 64-byte load instead of a chain of gathers: its id,
+// cluster, destination, degree, hash and graph base, ordering bucket,
+// mu w(v), Lambda, row start and delta_v.
+struct __align__(16) AbWork {
+  int32_t v, C, D, deg;
+  uint32_t hv;
+  int32_t vbase;
+  long long q, muw, Lam, beg, delta;
+};
+
 // Device-resident counters of one call (all graphs of a batch together).
 struct Scalars {
   int empty_movers;      // movers to a new empty cluster in this pass

@@ -210,9 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_ref_choose(LevelGraph g, const Gra
     uint64_t best = ~0ull;
     int32_t h = v;
     if (inU) {
-      // v's own draw lies in the top 2^-16 of the range: v keeps no edge
-      // only rarely when a neighbour qualifies, always when none does
-      best = (stream_rand(seed, level, 0, ((int64_t)v << 32) | v) >> 16) | (0xFFFFull << 48);
+      best = stream_rand(seed, level, 0, ((int64_t)v << 32) | v);
       for (int64_t e = g.rp[v] + r; e < g.rp[v + 1]; e += GS) {
         const int32_t u = __ldg(g.col + e);
         const RefRec ru = rec[u];  // one gather: B[u], u in U, w(u)

@@ -703,19 +703,35 @@ __global__ void __launch_bounds__(256) k_ab_prep(PassArgs a) {
     const int64_t w0 = base + (threadIdx.x & ~31);  // first id of this warp
     bool isc = false;
     int grp = -1;
+    AbWork wk;
     if (v < a.g.n) {
       AbRec r;
       r.C = a.C[v];
       r.D = a.D[v];
       isc = r.D != kNone;
-      r.q = isc ? eps_bucket(a.m, a.gp[graph_of(a, (int32_t)v)].Lam, a.delta[v]) : 0;
+      const GraphParam P = a.gp[graph_of(a, (int32_t)v)];
+      long long dv = 0;
+      if (isc) dv = a.delta[v];
+      r.q = isc ? eps_bucket(a.m, P.Lam, dv) : 0;
       a.ab[v] = r;
       a.M[v] = 0;  // survivors are set by the afterburner kernels
       if (isc) {
-        const int64_t deg = a.g.rp[v + 1] - a.g.rp[v];
+        const int64_t beg = a.g.rp[v];
+        const int64_t deg = a.g.rp[v + 1] - beg;
         cand += deg;
         for (int k = 0; k < kAbGroups && grp < 0; ++k)
           if (deg <= a.ab_max[k]) grp = k;  // hubs stay unlisted (grp -1)
+        wk.v = (int32_t)v;
+        wk.C = r.C;
+        wk.D = r.D;
+        wk.deg = (int32_t)deg;
+        wk.vbase = P.vbase;
+        wk.hv = fmix32((uint32_t)((int32_t)v - P.vbase) ^ a.m.seed);  // the id within its graph
+        wk.q = r.q;
+        wk.muw = P.mu * a.g.vw[v];
+        wk.Lam = P.Lam;
+        wk.beg = beg;
+        wk.delta = dv;
       }
     }
     const unsigned bits = __ballot_sync(0xFFFFFFFFu, isc);
@@ -726,7 +742,7 @@ __global__ void __launch_bounds__(256) k_ab_prep(PassArgs a) {
       int pos = 0;
       if (lane == leader) pos = atomicAdd(&a.sc->ab_count[grp], __popc(peers));
       pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1u));
-      a.ab_list[a.ab_off[grp] + pos] = (int32_t)v;
+      a.ab_list[a.ab_off[grp] + pos] = wk;
     }
   }
   flush_block_sum(cand, &a.sc->cand_edges);
@@ -734,10 +750,11 @@ __global__ void __launch_bounds__(256) k_ab_prep(PassArgs a) {
 
 struct AbCtx {
   int32_t v, Cv, Dv, vbase;
-  long long qv, wv, mu, Lam;
+  long long qv, muw, Lam;
   uint32_t hv;
 };
 
+// A hub's context, gathered (hubs are not listed with work records).
 __device__ __forceinline__ AbCtx ab_ctx(const PassArgs &a, int32_t v) {
   const AbRec r = a.ab[v];
   AbCtx c;
@@ -745,13 +762,25 @@ __device__ __forceinline__ AbCtx ab_ctx(const PassArgs &a, int32_t v) {
   c.Cv = r.C;
   c.Dv = r.D;
   c.qv = r.q;
-  c.wv = a.g.vw[v];
   const GraphParam P = a.gp[graph_of(a, v)];
   c.vbase = P.vbase;
-  c.mu = P.mu;
+  c.muw = P.mu * a.g.vw[v];
   c.Lam = P.Lam;
   // the hash takes the id within the vertex's own graph
   c.hv = fmix32((uint32_t)(v - c.vbase) ^ a.m.seed);
+  return c;
+}
+
+__device__ __forceinline__ AbCtx ab_ctx(const AbWork &w) {
+  AbCtx c;
+  c.v = w.v;
+  c.Cv = w.C;
+  c.Dv = w.D;
+  c.qv = w.q;
+  c.vbase = w.vbase;
+  c.muw = w.muw;
+  c.Lam = w.Lam;
+  c.hv = w.hv;
   return c;
 }
 
@@ -765,7 +794,7 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
   const int32_t *__restrict__ col = a.g.col + e0;
   const int32_t *__restrict__ ew = a.g.ew + e0;
   const int len = (int)(e1 - e0);
-  const long long muw = c.mu * c.wv;
+  const long long muw = c.muw;
   for (int base = r; base < len; base += GS * U) {
     int32_t u[U], w[U];
     AbRec rec[U];
@@ -822,7 +851,7 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
 // list / *count: the candidates of one group, listed by k_ab_prep.
 template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 4)
-    k_afterburner(PassArgs a, const int32_t *__restrict__ list, const int *__restrict__ count_ptr) {
+    k_afterburner(PassArgs a, const AbWork *__restrict__ list, const int *__restrict__ count_ptr) {
   constexpr int U = 4;
   long long cntM = 0;
   const int r = Grp<GS>::rank();
@@ -834,16 +863,16 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 
     __shared__ long long rs[2][GS / 32];
     int par = 0;
     for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
-      const int32_t v = list[i];
-      const AbCtx c = ab_ctx(a, v);
-      long long acc = warp_sum(ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r));
+      const AbWork wk = list[i];
+      const AbCtx c = ab_ctx(wk);
+      long long acc = warp_sum(ab_edges<GS, U>(a, c, wk.beg, wk.beg + wk.deg, r));
       if ((threadIdx.x & 31) == 0) rs[par][threadIdx.x >> 5] = acc;
       __syncthreads();
       if (threadIdx.x == 0) {
         long long t = 0;
         for (int w = 0; w < GS / 32; ++w) t += rs[par][w];
-        const bool keep = a.delta[v] + t >= 0;
-        a.M[v] = keep;
+        const bool keep = wk.delta + t >= 0;
+        a.M[wk.v] = keep;
         cntM += keep;
       }
       par ^= 1;
@@ -851,16 +880,17 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256, GS > 32 ? 2048 / GS / 2 : 
   } else {
     __shared__ long long rs[1];
     for_each_vertex<GS>(count, [&](int64_t i, bool active) {
-      const int32_t v = active ? list[i] : 0;
+      AbWork wk;
       long long acc = 0;
       if (active) {
-        const AbCtx c = ab_ctx(a, v);
-        acc = ab_edges<GS, U>(a, c, a.g.rp[v], a.g.rp[v + 1], r);
+        wk = list[i];
+        const AbCtx c = ab_ctx(wk);
+        acc = ab_edges<GS, U>(a, c, wk.beg, wk.beg + wk.deg, r);
       }
       acc = Grp<GS>::sum(acc, rs);
       if (active && r == 0) {
-        const bool keep = a.delta[v] + acc >= 0;
-        a.M[v] = keep;
+        const bool keep = wk.delta + acc >= 0;
+        a.M[wk.v] = keep;
         cntM += keep;
       }
     });

@@ -41,7 +41,7 @@ struct PassArgs {
   // afterburner: candidate bitmap (bit v of word v / 32) and the candidates
   // of each group, listed by the record pass into ab_list[ab_off[g] ...)
   uint32_t *inL;
-  int32_t *ab_list;
+  AbWork *ab_list;
   int64_t ab_off[kAbGroups];  // start of group g (the offset of its first bin)
   int64_t ab_max[kAbGroups];  // largest degree in group g (BinPlan)
   int32_t ab_gs[kAbGroups];   // threads per candidate in group g (BinPlan)

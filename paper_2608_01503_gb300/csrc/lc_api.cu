@@ -302,7 +302,7 @@ static int64_t level0_scratch_bytes(int64_t n0, int64_t nnz0, int64_t G, int tab
 }
 static int64_t level_bytes(int64_t n, int64_t nnz, int64_t G, const BinPlan &p) {
   const int64_t hubs = nnz / (p.hub_min() + 1) + 1, chunks = nnz / p.hub_chunk + hubs;
-  return 4 * n + 4 * (kBins + 1) + 40 * chunks + 36 * hubs  // bins, hub plan
+  return 4 * n + (int64_t)sizeof(VRec) * n + 4 * (kBins + 1) + 40 * chunks + 36 * hubs  // bins, hub plan
          + (int64_t)sizeof(GraphParam) * G                   // upload_params
          + 4 * n + (G > 1 ? 4 * n : 0)                      // Cd, next level's gid
          + 16 * (n + 1) + 8 * nnz;                          // coarse row_ptr, vw, col, ew
@@ -320,12 +320,14 @@ int64_t cluster_footprint(int64_t n, int64_t nnz, int count, const lc_opts &o) {
 static int bins_for(Run &r, Level &L) {
   LC_TRY(r.ar.get(&L.bins.lists, L.g.n));
   LC_TRY(r.ar.get(&L.bins.offs, kBins + 1));
+  LC_TRY(r.ar.get(&L.bins.recs, L.g.n));
   build_bins(L.g, r.plan, L.bins, r.scan32, r.s);
+  launch_vertex_records(L.g, L.gid, L.bins, r.s);
   int32_t h[kBins + 1];
   LC_CK(cudaMemcpyAsync(h, L.bins.offs, sizeof(h), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
   finish_bins(L.bins, h);
-  r.res->kernel_launches[LC_K_OTHER] += 4 * kBins;
+  r.res->kernel_launches[LC_K_OTHER] += 4 * kBins + 1;
   L.hub = Hubs{};
   const int H = (int)L.bins.count[kHubBin];
   if (H > 0) {

@@ -122,6 +122,16 @@ struct Method {
   uint32_t seed;
 };
 
+// A vertex of a level as the per-vertex kernels need it, stored in bin order
+// beside the bin lists once per level: its id, degree, graph and row start,
+// and w(v), so that a kernel reads its vertex in one coalesced 32-byte load
+// instead of a chain of gathers through the list entry.
+struct __align__(16) VRec {
+  int32_t v, deg, g, pad;
+  int64_t beg;
+  long long w;
+};
+
 // Afterburner record of a vertex for one pass: its cluster, destination and
 // priority bucket packed into one 16-byte load.
 struct __align__(16) AbRec {

@@ -96,16 +96,18 @@ __device__ __forceinline__ void first_edge(const PassArgs &a, const GraphParam &
 
 template <int GS>
 __global__ void __launch_bounds__(GS > 32 ? GS : 256)
-    k_first_pass(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
+    k_first_pass(PassArgs a, const VRec *__restrict__ rec, int64_t count) {
   __shared__ long long rg[GS > 32 ? GS / 32 : 1];
   __shared__ int32_t rx[GS > 32 ? GS / 32 : 1];
   long long cntL = 0;
   const int r = Grp<GS>::rank();
   for_each_vertex<GS>(count, [&](int64_t i, bool active) {
-    const int32_t v = active ? list[i] : 0;
-    const int64_t beg = active ? a.g.rp[v] : 0, end = active ? a.g.rp[v + 1] : 0;
-    const long long wv = active ? a.g.vw[v] : 0;
-    const GraphParam P = a.gp[graph_of(a, v)];
+    VRec vr{};
+    if (active) vr = rec[i];
+    const int32_t v = vr.v;
+    const int64_t beg = vr.beg, end = vr.beg + vr.deg;
+    const long long wv = vr.w;
+    const GraphParam P = a.gp[vr.g];
     long long gb = LLONG_MIN;
     int32_t xb = kNone;
 #pragma unroll 4
@@ -120,18 +122,19 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
 
 // One thread per vertex of degree <= 8: neighbour clusters and weights are
 // held in registers; S(v, X) for each distinct X is an unrolled compare-sum.
-__global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const int32_t *__restrict__ list,
+__global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const VRec *__restrict__ rec,
                                                         int64_t count) {
   constexpr int K = 8;
   long long cntL = 0, phi = 0, nX = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = list[i];
-    const int64_t beg = a.g.rp[v];
-    const int deg = (int)(a.g.rp[v + 1] - beg);
+    const VRec vr = rec[i];
+    const int32_t v = vr.v;
+    const int64_t beg = vr.beg;
+    const int deg = vr.deg;
     const int32_t Cv = a.C[v];
-    const long long wv = a.g.vw[v];
-    const GraphParam P = a.gp[graph_of(a, v)];
+    const long long wv = vr.w;
+    const GraphParam P = a.gp[vr.g];
     int32_t u[K], w[K], X[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const int32_
 // per-lane shared slot of the lowest matching lane.  S(v, C[v]) is a group
 // reduction (the dedicated current-cluster slot of Section IV-A-3).
 template <int G>
-__global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *__restrict__ list,
+__global__ void __launch_bounds__(256) k_move_small(PassArgs a, const VRec *__restrict__ rec,
                                                     int64_t count) {
   __shared__ int32_t acc[256];
   long long cntL = 0, phi = 0, nX = 0;
@@ -199,11 +202,13 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const int32_t *_
   const int sub = lane & (G - 1);
   const int wbase = threadIdx.x & ~31;
   for_each_vertex<G>(count, [&](int64_t i, bool active) {
-    const int32_t v = active ? list[i] : 0;
-    const int64_t beg = active ? a.g.rp[v] : 0, deg = active ? a.g.rp[v + 1] - beg : 0;
+    VRec vr{};
+    if (active) vr = rec[i];
+    const int32_t v = vr.v;
+    const int64_t beg = vr.beg, deg = vr.deg;
     const int32_t Cv = active ? a.C[v] : 0;
-    const long long wv = active ? a.g.vw[v] : 0;
-    const GraphParam P = a.gp[graph_of(a, v)];
+    const long long wv = vr.w;
+    const GraphParam P = a.gp[vr.g];
     const bool has = sub < deg;
     int32_t X = -1, w = 0;
     if (has) {
@@ -430,7 +435,7 @@ __device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam
 // slots.
 template <int SLOTS>
 __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
-    k_move_warp(PassArgs a, const int32_t *__restrict__ list, int64_t count) {
+    k_move_warp(PassArgs a, const VRec *__restrict__ rec, int64_t count) {
   constexpr int U = SLOTS / 128;  // edges per lane per batch: 64 (bin 3) or 128 (bin 4)
   __shared__ uint32_t keys[kWarpBinWarps][SLOTS];
   __shared__ int32_t vals[kWarpBinWarps][SLOTS];
@@ -444,11 +449,12 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
   __syncwarp();
   for_each_vertex<32>(count, [&](int64_t i, bool active) {
     if (!active) return;  // warp-uniform: the whole warp shares i
-    const int32_t v = list[i];
-    const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
+    const VRec vr = rec[i];
+    const int32_t v = vr.v;
+    const int64_t beg = vr.beg, end = vr.beg + vr.deg;
     const int32_t Cv = a.C[v];
-    const long long wv = a.g.vw[v];
-    const GraphParam P = a.gp[graph_of(a, v)];
+    const long long wv = vr.w;
+    const GraphParam P = a.gp[vr.g];
     const uint32_t cap = warp_table_cap(end - beg);
     bool ok = true;
     long long self = split_insert_row<32, U>(a, beg, end, Cv, tab, cap, lane, ok);
@@ -479,7 +485,7 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
 // BUILD: the tables use the kept-table layout (tab_cap slots) and are
 // copied out to each vertex's gtab region with S(v, C[v]) added.
 template <int GS, int SLOTS, bool BUILD>
-__global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__restrict__ list,
+__global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const VRec *__restrict__ rec,
                                                    int64_t count) {
   extern __shared__ uint32_t smem_tab[];
   const SplitTab tab{smem_tab, reinterpret_cast<int32_t *>(smem_tab + SLOTS)};
@@ -497,11 +503,12 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const int32_t *__
   }
   __syncthreads();
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
-    const int32_t v = list[i];
-    const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
+    const VRec vr = rec[i];
+    const int32_t v = vr.v;
+    const int64_t beg = vr.beg, end = vr.beg + vr.deg;
     const int32_t Cv = a.C[v];
-    const long long wv = a.g.vw[v];
-    const GraphParam P = a.gp[graph_of(a, v)];
+    const long long wv = vr.w;
+    const GraphParam P = a.gp[vr.g];
     const uint32_t cap = BUILD ? tab_cap(end - beg) : min(warp_table_cap(end - beg), (uint32_t)SLOTS);
     bool ok = true;
     long long self = split_insert_row<GS, 4>(a, beg, end, Cv, tab, cap, threadIdx.x, ok);
@@ -1483,8 +1490,29 @@ void build_bins(const LevelGraph &g, const BinPlan &plan, Bins &b, int32_t *scan
 void finish_bins(Bins &b, const int32_t *h_offs) {
   for (int k = 0; k < kBins; ++k) {
     b.list[k] = b.lists + h_offs[k];
+    b.rec[k] = b.recs + h_offs[k];
     b.count[k] = h_offs[k + 1] - h_offs[k];
   }
+}
+
+__global__ void k_vertex_records(LevelGraph g, const int32_t *__restrict__ gid, const int32_t *__restrict__ lists,
+                                 VRec *__restrict__ recs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = lists[i];
+    VRec r;
+    r.v = v;
+    r.beg = g.rp[v];
+    r.deg = (int32_t)(g.rp[v + 1] - r.beg);
+    r.g = gid ? gid[v] : 0;
+    r.pad = 0;
+    r.w = g.vw[v];
+    recs[i] = r;
+  }
+}
+
+void launch_vertex_records(const LevelGraph &g, const int32_t *gid, Bins &b, cudaStream_t s) {
+  if (g.n > 0) k_vertex_records<<<blocks_for(g.n, 256), 256, 0, s>>>(g, gid, b.lists, b.recs);
 }
 
 void launch_hub_rows(const int64_t *rp, const int32_t *vtx, int H, int64_t *out, cudaStream_t s) {
@@ -1492,12 +1520,23 @@ void launch_hub_rows(const int64_t *rp, const int32_t *vtx, int H, int64_t *out,
 }
 
 template <int GS>
-static int launch_vertex_kernel(void (*k)(PassArgs, const int32_t *, int64_t), const PassArgs &a,
+static int launch_vertex_kernel(void (*k)(PassArgs, const VRec *, int64_t), const PassArgs &a,
                                 BinRange r, cudaStream_t s, size_t smem = 0) {
   if (r.count <= 0) return 0;
   const int threads = GS > 32 ? GS : 256;
   const int per_block = GS > 32 ? 1 : threads / GS;
-  k<<<blocks_for(r.count, per_block), threads, smem, s>>>(a, r.list, r.count);
+  k<<<blocks_for(r.count, per_block), threads, smem, s>>>(a, r.rec, r.count);
+  return 1;
+}
+
+// The same over the plain vertex list (kernels that need little of a record).
+template <int GS>
+static int launch_list_kernel(void (*k)(PassArgs, const int32_t *, int64_t), const PassArgs &a, BinRange r,
+                              cudaStream_t s) {
+  if (r.count <= 0) return 0;
+  const int threads = GS > 32 ? GS : 256;
+  const int per_block = GS > 32 ? 1 : threads / GS;
+  k<<<blocks_for(r.count, per_block), threads, 0, s>>>(a, r.list, r.count);
   return 1;
 }
 
@@ -1524,10 +1563,10 @@ template <int GS, int SLOTS>
 static int launch_move_block(const PassArgs &a, BinRange r, cudaStream_t s) {
   if (r.count <= 0) return 0;
   if (a.tab_build)
-    k_move_block<GS, SLOTS, true><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.list,
+    k_move_block<GS, SLOTS, true><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.rec,
                                                                                                r.count);
   else
-    k_move_block<GS, SLOTS, false><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.list,
+    k_move_block<GS, SLOTS, false><<<blocks_for(r.count, 1), GS, block_table_bytes(SLOTS), s>>>(a, r.rec,
                                                                                                 r.count);
   return 1;
 }
@@ -1535,7 +1574,7 @@ static int launch_move_block(const PassArgs &a, BinRange r, cudaStream_t s) {
 template <int SLOTS>
 static int launch_move_warp(const PassArgs &a, BinRange r, cudaStream_t s) {
   if (r.count <= 0) return 0;
-  k_move_warp<SLOTS><<<blocks_for(r.count, kWarpBinWarps), kWarpBinWarps * 32, 0, s>>>(a, r.list, r.count);
+  k_move_warp<SLOTS><<<blocks_for(r.count, kWarpBinWarps), kWarpBinWarps * 32, 0, s>>>(a, r.rec, r.count);
   return 1;
 }
 
@@ -1544,7 +1583,7 @@ static int launch_move_low(const PassArgs &a, const Bins &b, cudaStream_t s) {
   int n = 0;
   const BinRange r0 = bin_range(b, 0, 0);
   if (r0.count > 0) {
-    k_move_thread<<<blocks_for(r0.count, 256), 256, 0, s>>>(a, r0.list, r0.count);
+    k_move_thread<<<blocks_for(r0.count, 256), 256, 0, s>>>(a, r0.rec, r0.count);
     n++;
   }
   n += launch_vertex_kernel<16>(k_move_small<16>, a, bin_range(b, 1, 1), s);
@@ -1673,11 +1712,11 @@ int launch_symmetry_ablation(const PassArgs &a, bool mlh, int32_t *size, cudaStr
 
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s) {
   int n = 0;
-  n += launch_vertex_kernel<1>(k_objective<1>, a, bin_range(b, 0, 0), s);
-  n += launch_vertex_kernel<16>(k_objective<16>, a, bin_range(b, 1, 1), s);
-  n += launch_vertex_kernel<32>(k_objective<32>, a, bin_range(b, 2, 4), s);
-  n += launch_vertex_kernel<128>(k_objective<128>, a, bin_range(b, 5, 6), s);
-  n += launch_vertex_kernel<512>(k_objective<512>, a, bin_range(b, 7, 8), s);
+  n += launch_list_kernel<1>(k_objective<1>, a, bin_range(b, 0, 0), s);
+  n += launch_list_kernel<16>(k_objective<16>, a, bin_range(b, 1, 1), s);
+  n += launch_list_kernel<32>(k_objective<32>, a, bin_range(b, 2, 4), s);
+  n += launch_list_kernel<128>(k_objective<128>, a, bin_range(b, 5, 6), s);
+  n += launch_list_kernel<512>(k_objective<512>, a, bin_range(b, 7, 8), s);
   if (a.hub.H > 0) {
     k_hub_objective<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     k_hub_obj_final<<<hub_final_blocks(a.hub.H), 256, 0, s>>>(a);

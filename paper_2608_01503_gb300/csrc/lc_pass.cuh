@@ -51,17 +51,20 @@ struct PassArgs {
 struct Bins {
   int32_t *lists;    // device, n entries, bin after bin
   int32_t *offs;     // device, kBins + 1 entries
+  VRec *recs;        // device, n entries: the vertex records of `lists`, same order
   const int32_t *list[kBins];
+  const VRec *rec[kBins];
   int64_t count[kBins];
 };
 
 // Bins are stored one after the other, so a run of bins is one list.
 struct BinRange {
   const int32_t *list;
+  const VRec *rec;
   int64_t count;
 };
 inline BinRange bin_range(const Bins &b, int lo, int hi) {
-  BinRange r{b.list[lo], 0};
+  BinRange r{b.list[lo], b.rec[lo], 0};
   for (int k = lo; k <= hi; ++k) r.count += b.count[k];
   return r;
 }
@@ -71,6 +74,8 @@ void configure_kernels();
 // and fills b.list / b.count (see finish_bins).
 void build_bins(const LevelGraph &g, const BinPlan &plan, Bins &b, int32_t *scan_tmp, cudaStream_t s);
 void finish_bins(Bins &b, const int32_t *h_offs);
+// Fills b.recs from b.lists (gid: graph of each vertex, or null for one graph).
+void launch_vertex_records(const LevelGraph &g, const int32_t *gid, Bins &b, cudaStream_t s);
 
 // Launchers return the number of kernels they launched.
 void launch_hub_rows(const int64_t *rp, const int32_t *vtx, int H, int64_t *out, cudaStream_t s);

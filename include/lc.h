@@ -444,6 +444,34 @@ LC_API int lc_objective_static(const lc_csr *g, const int64_t *vertex_w, const i
 /* Largest vertex count lc_objective_static accepts. */
 LC_API int64_t lc_objective_static_max_vertices(void);
 
+/* ---------------------------------------------------------------- checked build
+ * The paper has no counterpart: these support debugging the library itself.
+ * The library can be built with -DLC_DEBUG=1 (the Python binding's
+ * build(debug=True), loaded when LC_DEBUG=1 is set in the environment).
+ * That build checks, in every local-move, afterburner, update, objective and
+ * contraction kernel, each index it follows against the array it addresses:
+ * neighbour ids read from col against [0, n), cluster labels read from C and
+ * from hash tables against [0, n), destinations D[v] against [0, n), coarse
+ * ids against [0, n_c); hash probe sequences are bounded by their table's
+ * capacity in both builds.  A failed check neither faults nor stops the
+ * kernel: the index is replaced by 0, the first failure is recorded, and the
+ * call returns LC_ERR_DEVICE with res->error_detail = site << 56 | index
+ * (low 56 bits), site 1 column, 2 label, 3 destination, 4 probe overrun
+ * (index = the vertex, -1 for a kept table's rebuild), 5 coarse id.  The
+ * records are per process: calls running concurrently in the checked build
+ * (server slots, several threads) may report one another's failures.  On
+ * valid inputs both builds compute identical results; the checked build is
+ * slower.
+ *
+ * lc_debug_enabled: 1 in the checked build, else 0.
+ * lc_debug_selftest: checked build only (else LC_ERR_ARG): launches one
+ * thread that fails one check on purpose (index 7 against bound 3, without
+ * addressing memory) on `stream` (a cudaStream_t, null: the legacy default
+ * stream), collects the records and returns LC_OK if exactly that failure
+ * came back, with its encoded form in *detail (may be null). */
+LC_API int lc_debug_enabled(void);
+LC_API int lc_debug_selftest(void *stream, int64_t *detail);
+
 #ifdef __cplusplus
 }
 #endif

@@ -135,11 +135,12 @@ EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
            "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
            "lc_server_wait", "lc_server_destroy", "lc_server_cancel", "lc_release_memory",
-           "lc_scratch_estimate", "lc_autotune"]
+           "lc_scratch_estimate", "lc_autotune", "lc_debug_enabled", "lc_debug_selftest"]
 
 
 def library_path() -> str:
-    return _build.LIB
+    """liblc.so, or the checked build liblc_debug.so when LC_DEBUG=1 is set."""
+    return _build.lib_path()
 
 
 def load(build_if_missing: bool = True):
@@ -147,11 +148,12 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if not os.path.exists(path) or not _build.up_to_date():
+    debug = _build.debug_requested()
+    path = _build.lib_path(debug)
+    if not os.path.exists(path) or not _build.up_to_date(debug):
         if not build_if_missing:
-            raise RuntimeError(f"liblc.so not built at {path}")
-        _build.build()
+            raise RuntimeError(f"{os.path.basename(path)} not built at {path}")
+        _build.build(debug=debug)
     lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     i64, i32 = ctypes.c_int64, ctypes.c_int32
@@ -178,6 +180,10 @@ def load(build_if_missing: bool = True):
     lib.lc_scratch_estimate.restype = ctypes.c_int64
     lib.lc_autotune.argtypes = [csr, P, P, i32, P, P, P, opts, i32, ctypes.POINTER(_Tuning)]
     lib.lc_autotune.restype = ctypes.c_int
+    lib.lc_debug_enabled.argtypes = []
+    lib.lc_debug_enabled.restype = ctypes.c_int
+    lib.lc_debug_selftest.argtypes = [P, ctypes.POINTER(i64)]
+    lib.lc_debug_selftest.restype = ctypes.c_int
     srv = ctypes.c_void_p
     lib.lc_server_default_config.argtypes = [ctypes.POINTER(_ServerConfig)]
     lib.lc_server_default_config.restype = None
@@ -599,6 +605,22 @@ def save_tuning(key: str, tuning: dict, path: str = TUNING_CACHE) -> None:
 def lc_release_memory() -> None:
     """Returns the blocks cached in liblc's private pool on the current device."""
     _check(load().lc_release_memory())
+
+
+def lc_debug_enabled() -> bool:
+    """True when the loaded library is the checked build (LC_DEBUG=1)."""
+    return bool(load().lc_debug_enabled())
+
+
+def lc_debug_selftest(stream=None) -> int:
+    """Checked build: one deliberate index-check failure, collected and
+    decoded by the library; returns the encoded detail (site << 56 | index)."""
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    detail = ctypes.c_int64(0)
+    _check(load().lc_debug_selftest(ctypes.c_void_p(s.cuda_stream), ctypes.byref(detail)), detail.value)
+    return int(detail.value)
 
 
 def lc_objective_static_max_vertices() -> int:

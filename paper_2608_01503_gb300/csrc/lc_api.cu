@@ -16,6 +16,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lc_constraint.cuh"
 #include "lc_contract.cuh"
 #include "lc_leiden.cuh"
@@ -44,6 +46,16 @@ namespace lc {
     int rc_ = (expr);       \
     if (rc_ != LC_OK) return rc_; \
   } while (0)
+
+// NVTX range over a phase of a call (levels, local moves, contraction,
+// uncoarsening, pLeiden refinement) for timeline tools; without a tool
+// attached a push / pop is a null check.
+struct Phase {
+  explicit Phase(const char *name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase &) = delete;
+  Phase &operator=(const Phase &) = delete;
+};
 
 static int launch_check() {
   cudaError_t e = cudaGetLastError();
@@ -160,6 +172,7 @@ struct Run {
   Scalars *sc = nullptr;
   // per graph
   long long *phi_acc = nullptr, *phi_out = nullptr, *phi_trace = nullptr;
+  long long *obj = nullptr;  // [4 G] objective update after a call's last pass
   long long *Tg = nullptr, *Vg = nullptr, *sw2g = nullptr;
   int *improved = nullptr;
   int32_t *gstart = nullptr;
@@ -205,6 +218,7 @@ static int alloc_per_graph(Run &r) {
   LC_TRY(r.ar.get(&r.phi_acc, G));
   LC_TRY(r.ar.get(&r.phi_out, G));
   LC_TRY(r.ar.get(&r.phi_trace, G));
+  LC_TRY(r.ar.get(&r.obj, 4 * (int64_t)G));
   LC_TRY(r.ar.get(&r.Tg, G));
   LC_TRY(r.ar.get(&r.Vg, G));
   LC_TRY(r.ar.get(&r.sw2g, G));
@@ -289,7 +303,7 @@ static int resolve_plan(const lc_opts &o, BinPlan *out) {
 // upload_params, compact_level, contract_level), for the footprint below.
 static int64_t level0_scratch_bytes(int64_t n0, int64_t nnz0, int64_t G, int tables) {
   const int64_t n = n0 > 0 ? n0 : 1, big = 2 * nnz0 > n0 + 1 ? 2 * nnz0 : n0 + 1;
-  int64_t b = G * (6 * 8 + 4 + 4 + 1);                      // alloc_per_graph
+  int64_t b = G * (10 * 8 + 4 + 4 + 1);                     // alloc_per_graph
   b += 11 * 4 * n;                                           // C .. movers
   if (tables == 1) b += 2 * 4 * n + 8 * upd_list_size(n0, nnz0);
   b += 4 * scan_scratch(big);                                // scan32
@@ -420,6 +434,7 @@ static PassArgs pass_args(Run &r, const Level &L) {
   a.Cprev = r.Cprev;
   a.dirty = r.dirty;
   a.dirty_list = r.dirty_list;
+  a.obj = r.obj;
   a.hub_min = r.plan.hub_min();
   a.inL = r.inL;
   a.ab_list = r.ab_list;
@@ -511,6 +526,7 @@ static int capture_pass(Run &r, Level &L, const PassArgs &a, const ApplyScratch 
 // r.C_out and Phi(C_out) per graph in r.phi_out.
 static int local_move_passes(Run &r, Level &L, bool singleton, int level, int phase,
                              const std::vector<uint8_t> &active) {
+  Phase range("lc.local_move");
   const int64_t n = L.g.n, nnz = L.g.nnz;
   LC_TRY(upload_params(r, L, active));
   PassArgs a = pass_args(r, L);
@@ -534,8 +550,8 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
   const bool tables = r.o.tables == 1 && nnz > 0;
   bool kept = false;  // gtab holds tables matching C (updated by the next table pass)
   a.upd_list = tables ? r.upd_list : nullptr;
-  // one graph: the final objective is updated from the last pass (see below)
-  const bool incremental = r.G == 1;
+  // the final objective is updated from the last pass (see below)
+  const bool incremental = r.o.pass_limit >= 1;
   // opts.graphs: the repeated passes replay one captured pass; every pass
   // then reads its temperature from the device schedule
   bool capture = r.o.graphs == 1 && !r.prof.on && !(r.o.event_cb && r.G == 1) && !tables &&
@@ -604,9 +620,11 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
         kept = a.tab_build != 0;
         a.tab_build = 0;
       }
-      if (incremental && last) r.res->kernel_launches[LC_K_OBJECTIVE] += launch_save_phi_enter(a, r.s);
       r.prof.begin(LC_K_APPLY);
-      r.res->kernel_launches[LC_K_APPLY] += launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
+      r.res->kernel_launches[LC_K_APPLY] += launch_graph_sums(a, r.s);
+      // Phi entering the last pass, per graph, before the best-of test resets it
+      if (incremental && last) r.res->kernel_launches[LC_K_OBJECTIVE] += launch_save_phi_enter(a, r.s);
+      r.res->kernel_launches[LC_K_APPLY] += launch_bestof(a, r.C_out, r.s);
       r.prof.end(8.0 * n);
     }
     r.prof.begin(LC_K_AFTERBURNER);
@@ -625,9 +643,8 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
     if (r.o.event_cb && r.G == 1) LC_TRY(emit_pass_event(r, L, level, phase, i));
   }
   if (kept) LC_CK(cudaMemsetAsync(r.gtab, 0, 16 * (size_t)nnz, r.s));  // defensive: the last pass cleared them
-  // Phi of the final state for the best-of test: one graph updates it from
-  // the state entering the last pass and that pass's moves; a batch sweeps
-  // every graph
+  // Phi of the final state for the best-of test, updated per graph from
+  // the state entering the last pass and that pass's moves
   r.prof.begin(LC_K_OBJECTIVE);
   if (incremental) {
     r.res->kernel_launches[LC_K_OBJECTIVE] += launch_final_objective(a, r.s) + launch_bestof(a, r.C_out, r.s);
@@ -766,6 +783,7 @@ static int compact_level(Run &r, Level &L, Level &N, int level, bool *any) {
 
 // Algorithm 4 on (L.g, L.Cd) into N (whose n, vbase, nv, gid are set).
 static int contract_level(Run &r, Level &L, Level &N, int level) {
+  Phase range("lc.contract");
   const int64_t n_c = N.g.n;
   int64_t *rp_c = nullptr, *vw_c = nullptr;
   LC_TRY(r.ar.get(&rp_c, n_c + 1));
@@ -932,6 +950,14 @@ static int check_device_error(Run &r) {
   int err = 0;
   LC_CK(cudaMemcpyAsync(&err, &r.sc->error, sizeof(int), cudaMemcpyDeviceToHost, r.s));
   LC_CK(cudaStreamSynchronize(r.s));
+#if LC_DEBUG
+  // the checked build: the first failed index check of the call
+  DbgRecord f{};
+  if (dbg_collect(r.s, &f) > 0) {
+    r.res->error_detail = ((int64_t)f.site << 56) | (f.index & ((1ll << 56) - 1));
+    return LC_ERR_DEVICE;
+  }
+#endif
   return err ? LC_ERR_DEVICE : LC_OK;
 }
 
@@ -960,6 +986,7 @@ static int level0(Run &r, Level &L, const LevelGraph &g0, const std::vector<int6
 // ids 0..k-1 (numbered within the graph).
 static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t> &gptr,
                         int32_t *labels_out, const int32_t *B0 = nullptr) {
+  Phase call_range("lc.cluster");
   GraphStats st{};
   LC_TRY(alloc_per_graph(r));
   std::vector<Level> lv(1);
@@ -971,6 +998,7 @@ static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t>
   int top = 0;
   for (int l = 0;; ++l) {
     if (l >= kMaxLevels) return LC_ERR_TIMEOUT;
+    Phase level_range("lc.level");
     Level &L = lv[l];
     LC_TRY(bins_for(r, L));
     std::vector<uint8_t> present(r.G);
@@ -1004,6 +1032,7 @@ static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t>
   // clustering its last local-move call returned
   launch_iota(r.C_out, lv[top].g.n, r.s);
   for (int l = top - 1; l >= 0; --l) {
+    Phase up_range("lc.uncoarsen");
     Level &L = lv[l];
     // the level's parameters were last uploaded by its coarsening call
     launch_project(L.Cd, r.C_out, r.C, L.g.n, L.gid, L.gp, lv[l + 1].gp, r.s);
@@ -1158,6 +1187,7 @@ static int alloc_leiden(Run &r, int64_t n0, LeidenScratch &ls) {
 // refinement and Downsample.  A refinement that merges nothing also ends
 // the coarsening.
 static int pleiden_impl(Run &r, const LevelGraph &g0, const int32_t *C0, int32_t *labels_out) {
+  Phase call_range("lc.pleiden");
   GraphStats st{};
   LC_TRY(alloc_per_graph(r));
   std::vector<Level> lv(1);
@@ -1180,6 +1210,7 @@ static int pleiden_impl(Run &r, const LevelGraph &g0, const int32_t *C0, int32_t
   int top = 0;
   for (int l = 0;; ++l) {
     if (l >= kMaxLevels) return LC_ERR_TIMEOUT;
+    Phase level_range("lc.level");
     Level &L = lv[l];
     const int64_t n = L.g.n;
     LC_TRY(bins_for(r, L));
@@ -1218,9 +1249,12 @@ static int pleiden_impl(Run &r, const LevelGraph &g0, const int32_t *C0, int32_t
     // B = C_l with dense ids (ascending), its cluster weights, the refinement
     launch_relabel(r.C_out, r.newid, Bd, n, nullptr, r.gstart, nullptr, 0, r.s);
     launch_cluster_weights(Bd, L.g.vw, ls.WB, n, r.s);
-    r.prof.begin(LC_K_REFINE);
-    launch_pleiden_refine(L.g, L.bins, L.gp, Bd, r.o.seed, l, R, ls, &r.sc->error, r.s);
-    r.prof.end(64.0 * L.g.nnz + 200.0 * n);
+    {
+      Phase refine_range("lc.refine");
+      r.prof.begin(LC_K_REFINE);
+      launch_pleiden_refine(L.g, L.bins, L.gp, Bd, r.o.seed, l, R, ls, &r.sc->error, r.s);
+      r.prof.end(64.0 * L.g.nnz + 200.0 * n);
+    }
     r.res->kernel_launches[LC_K_REFINE] += 40;
     LC_TRY(launch_check());
     LC_CK(cudaMemcpyAsync(r.C_out, R, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, r.s));

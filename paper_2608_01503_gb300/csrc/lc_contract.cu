@@ -98,6 +98,7 @@ struct InsertArgs {
   unsigned long long *tab;
   int32_t *cnt;
   int *error;
+  int64_t nc;  // coarse vertices
 };
 
 // Insert fine edges [e0, e1) of v leaving C[v] into the coarse table of
@@ -119,12 +120,12 @@ __device__ __forceinline__ int insert_edges(const InsertArgs &a, int32_t x, int6
       u[k] = -1;
       w[k] = 0;
       if (e < e1) {
-        u[k] = __ldg(a.g.col + e);
+        u[k] = LC_IDX(__ldg(a.g.col + e), a.g.n, kDbgColumn);
         w[k] = __ldg(a.g.ew + e);
       }
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) y[k] = u[k] >= 0 ? a.Cd[u[k]] : x;
+    for (int k = 0; k < U; ++k) y[k] = u[k] >= 0 ? LC_IDX(a.Cd[u[k]], a.nc, kDbgCoarse) : x;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (y[k] == x) continue;
@@ -147,7 +148,10 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
     if (x < 0) return;  // graph finished coarsening
     bool ok = true;
     const int fresh_n = insert_edges<GS>(a, x, a.g.rp[v], a.g.rp[v + 1], r, ok);
-    if (!ok) *a.error = 1;
+    if (!ok) {
+      *a.error = 1;
+      LC_DBG_FAIL(kDbgProbe, v, a.g.n);
+    }
     if (fresh_n) atomicAdd(&a.cnt[x], fresh_n);
   });
 }
@@ -160,7 +164,10 @@ __global__ void __launch_bounds__(kHubThreads) k_insert_hub(InsertArgs a, Hubs h
   if (x < 0) return;  // graph finished coarsening
   bool ok = true;
   const int fresh_n = insert_edges<kHubThreads>(a, x, hub.e0[c], hub.e1[c], threadIdx.x, ok);
-  if (!ok) *a.error = 1;
+  if (!ok) {
+    *a.error = 1;
+    LC_DBG_FAIL(kDbgProbe, v, a.g.n);
+  }
   if (fresh_n) atomicAdd(&a.cnt[x], fresh_n);
 }
 
@@ -274,7 +281,7 @@ int launch_contract_insert(const LevelGraph &g, const int32_t *Cd, const int64_t
                            const int32_t *const *lists, const int64_t *counts, const Hubs &hub,
                            cudaStream_t s) {
   cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)(n_c > 0 ? n_c : 1), s);
-  InsertArgs a{g, Cd, off, tab, cnt, error};
+  InsertArgs a{g, Cd, off, tab, cnt, error, n_c};
   auto range = [&](int lo, int hi) {
     int64_t c = 0;
     for (int k = lo; k <= hi; ++k) c += counts[k];

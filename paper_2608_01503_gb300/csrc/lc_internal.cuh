@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "../../include/lc.h"
+#include "lc_debug.cuh"
 
 namespace lc {
 
@@ -164,18 +165,14 @@ struct Scalars {
   int upd_prev;          // ... by the last pass's (read by this pass's table update)
   int pad2;
   long long tab_rebuilt; // kept tables rebuilt, summed over the call's passes
-  // objective after a call's last pass (one graph), from the state entering it:
-  // Phi = Lam IN - mu Q with IN = sum_v S(v, C[v]), Q = sum_X W(X)^2 - sum_v w(v)^2
-  long long phi_enter;   // Phi entering the last pass (its move step's sum)
-  long long q_enter;     // Q entering the last pass
-  long long q_final;     // Q after it
-  long long d_in;        // change of IN by its moves
-  long long dphi_edges;  // movers' edges read for d_in, summed over the call
+  long long dphi_edges;  // movers' edges read for the objective update, summed over the call
   int n_movers;          // entries of PassArgs::movers
   int pad3;
   long long distinct_x;  // (vertex, adjacent cluster) pairs whose W(X) the move step read,
                          // summed over the call (the argmax's gathers, for the profile)
-  int ab_count[8];       // candidates listed per afterburner group in this pass
+  // candidates listed per afterburner group in this pass: per-warp atomics
+  // of the record pass, on a line of their own
+  alignas(128) int ab_count[8];
   // device-side temperature schedule (graph replays): k_pass_begin loads
   // phi_live from phi_tab[pass_idx] and advances pass_idx
   int pass_idx;

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const VRec *
     const int32_t v = vr.v;
     const int64_t beg = vr.beg;
     const int deg = vr.deg;
-    const int32_t Cv = a.C[v];
+    const int32_t Cv = LC_IDX(a.C[v], a.g.n, kDbgLabel);
     const long long wv = vr.w;
     const GraphParam P = a.gp[vr.g];
     int32_t u[K], w[K], X[K];
@@ -141,12 +141,12 @@ __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const VRec *
       u[j] = 0;
       w[j] = 0;
       if (j < deg) {
-        u[j] = __ldg(a.g.col + beg + j);
+        u[j] = LC_IDX(__ldg(a.g.col + beg + j), a.g.n, kDbgColumn);
         w[j] = __ldg(a.g.ew + beg + j);
       }
     }
 #pragma unroll
-    for (int j = 0; j < K; ++j) X[j] = j < deg ? a.C[u[j]] : -1;
+    for (int j = 0; j < K; ++j) X[j] = j < deg ? LC_IDX(a.C[u[j]], a.g.n, kDbgLabel) : -1;
     const long long WC = a.W[Cv];
     long long WX[K];
 #pragma unroll
@@ -206,15 +206,15 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const VRec *__re
     if (active) vr = rec[i];
     const int32_t v = vr.v;
     const int64_t beg = vr.beg, deg = vr.deg;
-    const int32_t Cv = active ? a.C[v] : 0;
+    const int32_t Cv = active ? LC_IDX(a.C[v], a.g.n, kDbgLabel) : 0;
     const long long wv = vr.w;
     const GraphParam P = a.gp[vr.g];
     const bool has = sub < deg;
     int32_t X = -1, w = 0;
     if (has) {
-      const int32_t u = __ldg(a.g.col + beg + sub);
+      const int32_t u = LC_IDX(__ldg(a.g.col + beg + sub), a.g.n, kDbgColumn);
       w = __ldg(a.g.ew + beg + sub);
-      X = a.C[u];
+      X = LC_IDX(a.C[u], a.g.n, kDbgLabel);
     }
     const long long WC = (active && sub == 0) ? a.W[Cv] : 0;
     const bool self = has && X == Cv;
@@ -279,7 +279,7 @@ __device__ __forceinline__ void range_argmax(const PassArgs &a, const GraphParam
       if (t[k] != kEmptySlot && !keep) tab[s] = kEmptySlot;
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) WX[k] = t[k] != kEmptySlot ? a.W[slot_key(t[k])] : 0;
+    for (int k = 0; k < U; ++k) WX[k] = t[k] != kEmptySlot ? a.W[LC_IDX(slot_key(t[k]), a.g.n, kDbgLabel)] : 0;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (t[k] == kEmptySlot) continue;
@@ -367,12 +367,12 @@ __device__ __forceinline__ long long split_insert_row(const PassArgs &a, int64_t
       u[k] = -1;
       w[k] = 0;
       if (e < deg) {
-        u[k] = __ldg(col + e);
+        u[k] = LC_IDX(__ldg(col + e), a.g.n, kDbgColumn);
         w[k] = __ldg(ew + e);
       }
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
+    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? LC_IDX(a.C[u[k]], a.g.n, kDbgLabel) : -1;
     bool todo[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
@@ -416,7 +416,7 @@ __device__ __forceinline__ void split_argmax(const PassArgs &a, const GraphParam
       }
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) WX[k] = key[k] != 0u ? a.W[key[k] - 1u] : 0;
+    for (int k = 0; k < U; ++k) WX[k] = key[k] != 0u ? a.W[LC_IDX(key[k] - 1u, a.g.n, kDbgLabel)] : 0;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       if (key[k] == 0u) continue;
@@ -452,13 +452,16 @@ __global__ void __launch_bounds__(kWarpBinWarps * 32, 4)
     const VRec vr = rec[i];
     const int32_t v = vr.v;
     const int64_t beg = vr.beg, end = vr.beg + vr.deg;
-    const int32_t Cv = a.C[v];
+    const int32_t Cv = LC_IDX(a.C[v], a.g.n, kDbgLabel);
     const long long wv = vr.w;
     const GraphParam P = a.gp[vr.g];
     const uint32_t cap = warp_table_cap(end - beg);
     bool ok = true;
     long long self = split_insert_row<32, U>(a, beg, end, Cv, tab, cap, lane, ok);
-    if (!ok) a.sc->error = 1;
+    if (!ok) {
+      a.sc->error = 1;
+      LC_DBG_FAIL(kDbgProbe, v, a.g.n);
+    }
     const long long WC = lane == 0 ? a.W[Cv] : 0;
     __syncwarp();
     long long gb = LLONG_MIN;
@@ -506,13 +509,16 @@ __global__ void __launch_bounds__(GS) k_move_block(PassArgs a, const VRec *__res
     const VRec vr = rec[i];
     const int32_t v = vr.v;
     const int64_t beg = vr.beg, end = vr.beg + vr.deg;
-    const int32_t Cv = a.C[v];
+    const int32_t Cv = LC_IDX(a.C[v], a.g.n, kDbgLabel);
     const long long wv = vr.w;
     const GraphParam P = a.gp[vr.g];
     const uint32_t cap = BUILD ? tab_cap(end - beg) : min(warp_table_cap(end - beg), (uint32_t)SLOTS);
     bool ok = true;
     long long self = split_insert_row<GS, 4>(a, beg, end, Cv, tab, cap, threadIdx.x, ok);
-    if (!ok) a.sc->error = 1;
+    if (!ok) {
+      a.sc->error = 1;
+      LC_DBG_FAIL(kDbgProbe, v, a.g.n);
+    }
     const long long WC = threadIdx.x == 0 ? a.W[Cv] : 0;
     __syncthreads();
     long long gb = LLONG_MIN;
@@ -581,7 +587,7 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
   const int h = a.hub.hub_of[c];
   const int32_t v = a.hub.vtx[h];
   const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
-  const int32_t Cv = a.C[v];
+  const int32_t Cv = LC_IDX(a.C[v], a.g.n, kDbgLabel);
   unsigned long long *tab = a.gtab + 2 * beg;
   const uint32_t cap = (uint32_t)(2 * (end - beg));
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
@@ -596,12 +602,12 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
       u[k] = -1;
       w[k] = 0;
       if (e < e1) {
-        u[k] = __ldg(a.g.col + e);
+        u[k] = LC_IDX(__ldg(a.g.col + e), a.g.n, kDbgColumn);
         w[k] = __ldg(a.g.ew + e);
       }
     }
 #pragma unroll
-    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? a.C[u[k]] : -1;
+    for (int k = 0; k < U; ++k) X[k] = u[k] >= 0 ? LC_IDX(a.C[u[k]], a.g.n, kDbgLabel) : -1;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const bool other = u[k] >= 0 && X[k] != Cv;
@@ -621,7 +627,10 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
       __syncwarp();
     }
   }
-  if (!ok) a.sc->error = 1;
+  if (!ok) {
+    a.sc->error = 1;
+    LC_DBG_FAIL(kDbgProbe, v, a.g.n);
+  }
   hub_acc_add(a, h, self);
 }
 
@@ -812,7 +821,7 @@ __device__ __forceinline__ long long ab_edges(const PassArgs &a, const AbCtx &c,
       u[k] = -1;
       w[k] = 0;
       if (e < len) {
-        u[k] = __ldg(col + e);
+        u[k] = LC_IDX(__ldg(col + e), a.g.n, kDbgColumn);
         w[k] = __ldg(ew + e);
       }
     }
@@ -947,7 +956,7 @@ __global__ void __launch_bounds__(GS > 32 ? GS : 256)
       Cv = a.C[v];
 #pragma unroll 4
       for (int64_t e = beg + r; e < end; e += GS)
-        if (a.C[__ldg(a.g.col + e)] == Cv) self += __ldg(a.g.ew + e);
+        if (a.C[LC_IDX(__ldg(a.g.col + e), a.g.n, kDbgColumn)] == Cv) self += __ldg(a.g.ew + e);
     }
     self = Grp<GS>::sum(self, rs);
     if (active && r == 0)
@@ -963,7 +972,7 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_objective(PassArgs a) {
   long long self = 0;
 #pragma unroll 4
   for (int64_t e = a.hub.e0[c] + threadIdx.x; e < a.hub.e1[c]; e += kHubThreads)
-    if (a.C[__ldg(a.g.col + e)] == Cv) self += __ldg(a.g.ew + e);
+    if (a.C[LC_IDX(__ldg(a.g.col + e), a.g.n, kDbgColumn)] == Cv) self += __ldg(a.g.ew + e);
   hub_acc_add(a, h, self);
 }
 
@@ -1090,12 +1099,16 @@ __global__ void __launch_bounds__(256) k_tab_rebuild(PassArgs a) {
     __syncwarp();
     for (int64_t e = beg + lane; e < beg + deg; e += 32) {
       bool fresh;
-      ok &= table_add(t, cap, a.C[__ldg(a.g.col + e)], __ldg(a.g.ew + e), fresh);
+      ok &= table_add(t, cap, LC_IDX(a.C[LC_IDX(__ldg(a.g.col + e), a.g.n, kDbgColumn)], a.g.n, kDbgLabel),
+                      __ldg(a.g.ew + e), fresh);
     }
     __syncwarp();
     if (lane == 0) a.dirty[v] = 0;
   }
-  if (!ok) a.sc->error = 1;
+  if (!ok) {
+    a.sc->error = 1;
+    LC_DBG_FAIL(kDbgProbe, -1, a.g.n);  // the table of one of this thread's listed vertices
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0 && cnt > 0) a.sc->tab_rebuilt += cnt;
 }
 
@@ -1232,8 +1245,8 @@ __global__ void k_apply(PassArgs a, uint8_t *__restrict__ E) {
         }
         atomicAdd((unsigned long long *)&a.W[Cv], (unsigned long long)(-wv));
         if (Dv >= 0) {
-          a.C[v] = Dv;
-          atomicAdd((unsigned long long *)&a.W[Dv], (unsigned long long)wv);
+          a.C[v] = LC_IDX(Dv, a.g.n, kDbgDest);
+          atomicAdd((unsigned long long *)&a.W[LC_IDX(Dv, a.g.n, kDbgDest)], (unsigned long long)wv);
         } else {
           e = 1;
           empties++;
@@ -1754,7 +1767,7 @@ __device__ __forceinline__ long long delta_in_edges(const PassArgs &a, int32_t v
       u[k] = -1;
       w[k] = 0;
       if (e < e1) {
-        u[k] = __ldg(a.g.col + e);
+        u[k] = LC_IDX(__ldg(a.g.col + e), a.g.n, kDbgColumn);
         w[k] = __ldg(a.g.ew + e);
       }
     }
@@ -1774,7 +1787,16 @@ __device__ __forceinline__ long long delta_in_edges(const PassArgs &a, int32_t v
   return d;
 }
 
-// dIN over the listed movers (degree <= 4096), one warp each.
+// The per-graph accumulators of the objective update: a.obj holds
+// [Phi entering | Q entering | Q after | dIN], G entries each.
+__device__ __forceinline__ long long *obj_phi_enter(const PassArgs &a) { return a.obj; }
+__device__ __forceinline__ long long *obj_q_enter(const PassArgs &a) { return a.obj + a.G; }
+__device__ __forceinline__ long long *obj_q_final(const PassArgs &a) { return a.obj + 2 * a.G; }
+__device__ __forceinline__ long long *obj_d_in(const PassArgs &a) { return a.obj + 3 * a.G; }
+
+// dIN over the listed movers (not hubs), one warp each; a batch (BATCH)
+// adds each mover's change to its own graph's sum.
+template <bool BATCH>
 __global__ void __launch_bounds__(256) k_delta_in(PassArgs a) {
   const int cnt = a.sc->n_movers;
   const int lane = threadIdx.x & 31;
@@ -1783,27 +1805,36 @@ __global__ void __launch_bounds__(256) k_delta_in(PassArgs a) {
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
     const int32_t v = a.movers[j];
     const int64_t beg = a.g.rp[v], end = a.g.rp[v + 1];
-    d += delta_in_edges<32>(a, v, beg, end, lane);
+    const long long dv = delta_in_edges<32>(a, v, beg, end, lane);
+    if constexpr (BATCH) {
+      const long long t = warp_sum(dv);
+      if (lane == 0 && t != 0) atomicAdd((unsigned long long *)&obj_d_in(a)[a.gid[v]], (unsigned long long)t);
+    } else {
+      d += dv;
+    }
     if (lane == 0) edges += end - beg;
   }
-  flush_block_sum(d, &a.sc->d_in);
+  if (!BATCH) flush_block_sum(d, obj_d_in(a));
   flush_block_sum(edges, &a.sc->dphi_edges);
 }
 
 __global__ void __launch_bounds__(kHubThreads) k_hub_delta_in(PassArgs a) {
+  __shared__ long long rs[kHubThreads / 32];
   const int c = blockIdx.x;
   const int32_t v = a.hub.vtx[a.hub.hub_of[c]];
   if (!a.M[v]) return;  // block-uniform
-  const long long d = delta_in_edges<kHubThreads>(a, v, a.hub.e0[c], a.hub.e1[c], threadIdx.x);
-  flush_block_sum(d, &a.sc->d_in);
-  if (threadIdx.x == 0) atomicAdd((unsigned long long *)&a.sc->dphi_edges,
-                                  (unsigned long long)(a.hub.e1[c] - a.hub.e0[c]));
+  const long long d =
+      Grp<kHubThreads>::sum(delta_in_edges<kHubThreads>(a, v, a.hub.e0[c], a.hub.e1[c], threadIdx.x), rs);
+  if (threadIdx.x == 0) {
+    if (d != 0) atomicAdd((unsigned long long *)&obj_d_in(a)[graph_of(a, v)], (unsigned long long)d);
+    atomicAdd((unsigned long long *)&a.sc->dphi_edges, (unsigned long long)(a.hub.e1[c] - a.hub.e0[c]));
+  }
 }
 
 // Q = sum_x W(x)^2 - w(x)^2 over the level's ids x (W of an unused id is 0)
-// into *q (zeroed by the caller).  Unsigned arithmetic: exact whenever Q
-// fits (mu > 0 and the guard Lam T + mu V^2 < 2^60); with mu = 0 it is
-// not used.
+// into q[0] (zeroed by the caller).  Unsigned arithmetic: exact whenever Q
+// fits (mu > 0 and the guard Lam T + mu V^2 < 2^60); with mu = 0 it is not
+// used.
 __global__ void k_q(PassArgs a, long long *q) {
   long long t = 0;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.g.n;
@@ -1814,39 +1845,83 @@ __global__ void k_q(PassArgs a, long long *q) {
   flush_block_sum(t, q);
 }
 
-__global__ void k_save_phi_enter(PassArgs a) { a.sc->phi_enter = a.phi_acc[0]; }
+// The same per graph of a batch, into q[g].  The labels of a graph lie in
+// its own vertex range, so the lanes of a warp cover a few runs of one graph
+// each; each run is summed by a segmented shuffle scan and added once.
+__global__ void k_q_batch(PassArgs a, long long *q) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.g.n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = base + threadIdx.x;
+    long long t = 0;
+    if (x < a.g.n) {
+      const unsigned long long W = (unsigned long long)a.W[x], w = (unsigned long long)a.g.vw[x];
+      t = (long long)(W * W - w * w);
+    }
+    const int g = x < a.g.n ? a.gid[x] : -1;
+    // inclusive scan within runs of equal g
+    const int gp = __shfl_up_sync(0xFFFFFFFFu, g, 1);
+    const bool head = lane == 0 || gp != g;
+    unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      // lanes o back are in the same run if no head lies in (lane - o, lane]
+      const unsigned span = (lane >= o) ? (((1u << lane) << 1) - (1u << (lane - o + 1))) : 0u;
+      if (lane >= o && (heads & span) == 0) t += y;
+    }
+    const int gn = __shfl_down_sync(0xFFFFFFFFu, g, 1);
+    const bool tail = lane == 31 || gn != g;
+    if (tail && g >= 0 && t != 0) atomicAdd((unsigned long long *)&q[g], (unsigned long long)t);
+  }
+}
+
+static void launch_q(const PassArgs &a, long long *q, cudaStream_t s) {
+  if (a.gid)
+    k_q_batch<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, q);
+  else
+    k_q<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, q);
+}
+
+__global__ void k_save_phi_enter(PassArgs a) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.G; g += gridDim.x * blockDim.x)
+    obj_phi_enter(a)[g] = a.phi_acc[g];
+}
 
 __global__ void k_final_phi(PassArgs a) {
-  const GraphParam P = a.gp[0];
-  const long long dq = a.sc->q_final - a.sc->q_enter;
-  a.phi_acc[0] = a.sc->phi_enter + P.Lam * a.sc->d_in - (P.mu != 0 ? P.mu * dq : 0);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.G; g += gridDim.x * blockDim.x) {
+    const GraphParam P = a.gp[g];
+    const long long dq = obj_q_final(a)[g] - obj_q_enter(a)[g];
+    a.phi_acc[g] = obj_phi_enter(a)[g] + P.Lam * obj_d_in(a)[g] - (P.mu != 0 ? P.mu * dq : 0);
+  }
 }
 
 int launch_last_pass_enter(const PassArgs &a, cudaStream_t s) {
-  cudaMemsetAsync(&a.sc->q_enter, 0, sizeof(long long), s);
-  if (a.g.n > 0) k_q<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, &a.sc->q_enter);
+  cudaMemsetAsync(a.obj + a.G, 0, sizeof(long long) * (size_t)a.G, s);
+  if (a.g.n > 0) launch_q(a, a.obj + a.G, s);
   return a.g.n > 0 ? 1 : 0;
 }
 
 int launch_save_phi_enter(const PassArgs &a, cudaStream_t s) {
-  k_save_phi_enter<<<1, 1, 0, s>>>(a);
+  k_save_phi_enter<<<blocks_for(a.G, 256), 256, 0, s>>>(a);
   return 1;
 }
 
 int launch_final_objective(const PassArgs &a, cudaStream_t s) {
-  cudaMemsetAsync(&a.sc->q_final, 0, sizeof(long long), s);
-  cudaMemsetAsync(&a.sc->d_in, 0, sizeof(long long), s);
-  k_delta_in<<<152 * 8, 256, 0, s>>>(a);
+  cudaMemsetAsync(a.obj + 2 * a.G, 0, 2 * sizeof(long long) * (size_t)a.G, s);  // Q after, dIN
+  if (a.gid)
+    k_delta_in<true><<<152 * 8, 256, 0, s>>>(a);
+  else
+    k_delta_in<false><<<152 * 8, 256, 0, s>>>(a);
   int n = 1;
   if (a.hub.H > 0) {
     k_hub_delta_in<<<a.hub.Q, kHubThreads, 0, s>>>(a);
     n++;
   }
   if (a.g.n > 0) {
-    k_q<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, &a.sc->q_final);
+    launch_q(a, a.obj + 2 * a.G, s);
     n++;
   }
-  k_final_phi<<<1, 1, 0, s>>>(a);
+  k_final_phi<<<blocks_for(a.G, 256), 256, 0, s>>>(a);
   return n + 1;
 }
 

@@ -36,7 +36,9 @@ struct PassArgs {
   int2 *upd_list;            // chunks {mover, chunk} of the movers' rows, listed by the
                              // apply step when tables are kept (else nullptr)
   int32_t *movers;           // movers that are not hubs, listed by the apply step of a
-                             // call's last pass (one graph; else nullptr), sc->n_movers
+                             // call's last pass (else nullptr), sc->n_movers
+  long long *obj;            // [4 G] per graph: Phi entering the last pass, Q entering it,
+                             // Q after it, change of IN by its moves (objective update)
   int64_t hub_min;           // rows longer than this are hubs (BinPlan::hub_min)
   // afterburner: candidate bitmap (bit v of word v / 32) and the candidates
   // of each group, listed by the record pass into ab_list[ab_off[g] ...)
@@ -92,11 +94,12 @@ int launch_afterburner(const PassArgs &a, const Bins &b, cudaStream_t s);
 // cluster with a larger label.  size: int32[n] scratch.
 int launch_symmetry_ablation(const PassArgs &a, bool mlh, int32_t *size, cudaStream_t s);
 int launch_objective(const PassArgs &a, const Bins &b, cudaStream_t s);
-// One graph only: the objective of the state after a call's last pass
-// from the state entering it.  launch_last_pass_enter runs at the start of
-// the last pass (Q of W before its update), launch_save_phi_enter after its
-// move step (Phi it summed), launch_final_objective after its update (the
-// movers' edges, Q after; needs the pass's M and Cprev): Phi into phi_acc[0].
+// The objective of each graph's state after a call's last pass, from the
+// state entering it.  launch_last_pass_enter runs at the start of the last
+// pass (Q of W before its update), launch_save_phi_enter after its move step
+// and per-graph sums (Phi entering), launch_final_objective after its update
+// (the movers' edges, Q after; needs the pass's M and Cprev): Phi into
+// phi_acc[g].
 int launch_last_pass_enter(const PassArgs &a, cudaStream_t s);
 int launch_save_phi_enter(const PassArgs &a, cudaStream_t s);
 int launch_final_objective(const PassArgs &a, cudaStream_t s);

@@ -119,3 +119,27 @@ def test_scratch_estimate_matches_the_driver_sizes(lib):
     assert lc.lc_scratch_estimate(1000, 10000, count=8) > a
     assert lib.lc_scratch_estimate(-1, 0, 1, None) == -1
     assert lib.lc_scratch_estimate(10, 0, 0, None) == -1
+
+
+def test_release_build_is_not_the_checked_build(lib):
+    """lc_debug_enabled is 0 and lc_debug_selftest refuses (LC_ERR_ARG)
+    before touching the device in the release build."""
+    assert lib.lc_debug_enabled() == 0
+    detail = ctypes.c_int64(-1)
+    assert lib.lc_debug_selftest(None, ctypes.byref(detail)) == 1
+    assert detail.value == 0
+
+
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    """The -DLC_DEBUG=1 build cross-compiles, exports every declared symbol
+    and reports itself as checked (host calls only)."""
+    from paper_2608_01503_gb300 import _build
+
+    path = _build.build(debug=True)
+    assert path.endswith("liblc_debug.so")
+    out = subprocess.check_output(["nm", "-D", "--defined-only", path]).decode()
+    exported = set(re.findall(r"\sT\s(\w+)$", out, re.M))
+    assert not [s for s in declared_symbols() if s not in exported]
+    dbg = ctypes.CDLL(path)
+    dbg.lc_debug_enabled.restype = ctypes.c_int
+    assert dbg.lc_debug_enabled() == 1

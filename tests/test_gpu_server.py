@@ -128,3 +128,27 @@ def test_scratch_limit_gives_oom_and_leaves_no_state():
         labels, res = lc.lc_cluster(*args, opts=lc.Options(scratch_limit=limit))
         torch.cuda.synchronize()
         assert np.array_equal(labels.cpu().numpy(), ref) and res["phi"] == ores["phi"]
+
+
+@pytest.mark.slow
+def test_small_request_finishes_during_a_long_job():
+    """A small request submitted while an R-MAT scale-21 job runs in another
+    slot is done before that job is; both equal their standalone results."""
+    big = gg.rmat(21, seed=11)
+    small = gg.sbm_planted(n=1500, blocks=15, p_in=0.08, p_out=0.003, seed=4)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    big_ref, big_res = lc.lc_cluster(t(big.row_ptr), t(big.col), t(big.ew), t(big.vw), big.lam_num, big.lam_den,
+                                     opts=lc.Options(allocator="library"))
+    big_ref = big_ref.cpu().numpy()
+    with lc.Server(slots=2, max_batch=8) as srv:
+        jb = srv.submit(big.row_ptr, big.col, big.ew, big.vw, big.lam_num, big.lam_den)
+        time.sleep(0.005)  # the long job is admitted to the first slot
+        js = srv.submit(small.row_ptr, small.col, small.ew, small.vw, small.lam_num, small.lam_den)
+        s_labels, s_res, s_lat = srv.wait(js)
+        assert srv.poll(jb) is None, "the long job finished before the small request"
+        b_labels, b_res, b_lat = srv.wait(jb)
+    assert s_lat < b_lat
+    ref, ores, _ = oracle.louvain_plus(small)
+    assert np.array_equal(s_labels, ref) and s_res["phi"] == ores["phi"]
+    assert np.array_equal(b_labels, big_ref) and b_res["phi"] == big_res["phi"]

@@ -700,7 +700,7 @@ __global__ void k_hub_decide(PassArgs a, int first) {
 
 // ------------------------------------------------ afterburner (Algorithm 3)
 
-// Packs {C, D, epsilon bucket of delta} per vertex for the afterburner's
+// Packs {C, D, epsilon bucket of delta} per candidate for the afterburner's
 // neighbour gathers (one 16-byte load each).  The bucket of Section IV-A-1,
 // floor(eps_den * delta / (eps_num * Lambda)), needs a 128-bit division; it
 // is done here, one thread per vertex, off the aggregation kernels.
@@ -722,16 +722,17 @@ __global__ void __launch_bounds__(256) k_ab_prep(PassArgs a) {
     AbWork wk;
     if (v < a.g.n) {
       AbRec r;
-      r.C = a.C[v];
       r.D = a.D[v];
       isc = r.D != kNone;
-      const GraphParam P = a.gp[graph_of(a, (int32_t)v)];
-      long long dv = 0;
-      if (isc) dv = a.delta[v];
-      r.q = isc ? eps_bucket(a.m, P.Lam, dv) : 0;
-      a.ab[v] = r;
       a.M[v] = 0;  // survivors are set by the afterburner kernels
       if (isc) {
+        // only candidates' records are ever read (the bitmap filters the
+        // neighbour gathers, hubs read their own only as candidates)
+        r.C = a.C[v];
+        const GraphParam P = a.gp[graph_of(a, (int32_t)v)];
+        const long long dv = a.delta[v];
+        r.q = eps_bucket(a.m, P.Lam, dv);
+        a.ab[v] = r;
         const int64_t beg = a.g.rp[v];
         const int64_t deg = a.g.rp[v + 1] - beg;
         cand += deg;

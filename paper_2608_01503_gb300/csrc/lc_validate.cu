@@ -68,73 +68,103 @@ __global__ void __launch_bounds__(256) k_stats_vertices(LevelGraph g, int valida
   }
 }
 
-// Per-edge part, load-balanced: each thread takes kChunk consecutive entries,
-// finds the row of the first by binary search on row_ptr and walks on.
-// Every index stays in range even for a malformed row_ptr (that case is
-// reported by the vertex part).
-__global__ void __launch_bounds__(256) k_stats_edges(LevelGraph g, int validate, GraphStats *st,
-                                                     const int32_t *gid, long long *Tg) {
-  constexpr int kChunk = 32;
-  const int64_t chunks = (g.nnz + kChunk - 1) / kChunk;
+// Per-edge part, load-balanced: each thread takes kStatsChunk consecutive
+// entries, finds the row of the first by binary search on row_ptr and walks
+// on.  A warp first copies its tile of 32 x kStatsChunk entries from col and
+// ew into shared memory with coalesced loads, transposed (row stride 33) so
+// that each thread then reads its own consecutive entries without bank
+// conflicts; reading them straight from global memory would touch 32 lines
+// per warp load.  Every index stays in range even for a malformed row_ptr
+// (that case is reported by the vertex part).
+constexpr int kStatsChunk = 32;
+constexpr int kStatsTile = 32 * kStatsChunk;  // entries per warp tile
+constexpr int kStatsThreads = 128;
+
+__global__ void __launch_bounds__(kStatsThreads) k_stats_edges(LevelGraph g, int validate, GraphStats *st,
+                                                               const int32_t *gid, long long *Tg) {
+  __shared__ int32_t s_col[kStatsThreads / 32][32 * 33];
+  __shared__ int32_t s_ew[kStatsThreads / 32][32 * 33];
+  const int lane = threadIdx.x & 31;
+  int32_t *tc = s_col[threadIdx.x >> 5];
+  int32_t *tw = s_ew[threadIdx.x >> 5];
+  const int64_t tiles = (g.nnz + kStatsTile - 1) / kStatsTile;
+  const int64_t nwarps = (int64_t)gridDim.x * (kStatsThreads / 32);
   long long T = 0;
   unsigned long long f1 = 0, f2 = 0;
-  for (int64_t cb = (int64_t)blockIdx.x * blockDim.x; cb < chunks;
-       cb += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = cb + threadIdx.x;
+  // warp-uniform loop over tiles
+  for (int64_t tile = (int64_t)blockIdx.x * (kStatsThreads / 32) + (threadIdx.x >> 5); tile < tiles;
+       tile += nwarps) {
+    const int64_t tb = tile * kStatsTile;
+    __syncwarp();  // the last tile's reads are done
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const int64_t e = tb + j * 32 + lane;
+      if (e < g.nnz) {
+        tc[j * 33 + lane] = g.col[e];
+        tw[j * 33 + lane] = g.ew[e];
+      }
+    }
+    __syncwarp();
     int cur_g = -1;      // graph of the edges summed into tg so far
     long long tg = 0;
-    if (c < chunks) {
-    const int64_t e0 = c * kChunk;
-    const int64_t e1 = e0 + kChunk < g.nnz ? e0 + kChunk : g.nnz;
-    int64_t lo = 0, hi = g.n;
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (g.rp[mid] <= e0)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    int64_t v = lo, vbeg = g.rp[v], vend = g.rp[v + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-      while (e >= vend && v + 1 < g.n) {
-        ++v;
-        vbeg = vend;
-        vend = g.rp[v + 1];
+    const int64_t e0 = tb + (int64_t)lane * kStatsChunk;
+    if (e0 < g.nnz) {
+      const int64_t e1 = e0 + kStatsChunk < g.nnz ? e0 + kStatsChunk : g.nnz;
+      int64_t lo = 0, hi = g.n;
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (g.rp[mid] <= e0)
+          lo = mid;
+        else
+          hi = mid;
       }
-      const int32_t u = g.col[e];
-      const int32_t w = g.ew[e];
-      T += w;
-      if (gid) {
-        const int gv = gid[v];
-        if (gv != cur_g && cur_g >= 0) {  // chunk crosses into the next graph
-          atomicAdd((unsigned long long *)&Tg[cur_g], (unsigned long long)tg);
-          tg = 0;
+      int64_t v = lo, vbeg = g.rp[v], vend = g.rp[v + 1];
+      for (int64_t e = e0; e < e1; ++e) {
+        while (e >= vend && v + 1 < g.n) {
+          ++v;
+          vbeg = vend;
+          vend = g.rp[v + 1];
         }
-        cur_g = gv;
-        tg += w;
-        if (validate && u >= 0 && u < g.n && gid[u] != gv) report(st, LC_ERR_ARG, v);
+        const int j = (int)(e - e0);
+        const int32_t u = tc[lane * 33 + j];
+        const int32_t w = tw[lane * 33 + j];
+        T += w;
+        if (gid) {
+          const int gv = gid[v];
+          if (gv != cur_g && cur_g >= 0) {  // chunk crosses into the next graph
+            atomicAdd((unsigned long long *)&Tg[cur_g], (unsigned long long)tg);
+            tg = 0;
+          }
+          cur_g = gv;
+          tg += w;
+          if (validate && u >= 0 && u < g.n && gid[u] != gv) report(st, LC_ERR_ARG, v);
+        }
+        if (!validate) continue;
+        if (u < 0 || u >= g.n) {
+          report(st, LC_ERR_ARG, v);
+          continue;
+        }
+        if (u == v) report(st, LC_ERR_SELF_LOOP, v);
+        if (e > vbeg) {
+          // the entry before e: this thread's, the previous thread's last
+          // one, or (first thread of the tile) global memory
+          const int32_t prev = j > 0 ? tc[lane * 33 + j - 1] : lane > 0 ? tc[(lane - 1) * 33 + 31] : g.col[e - 1];
+          if (prev >= u) report(st, LC_ERR_DUPLICATE, v);
+        }
+        if (w <= 0) report(st, LC_ERR_WEIGHT, v);
+        const unsigned long long a = (unsigned long long)(v < u ? v : u);
+        const unsigned long long b = (unsigned long long)(v < u ? u : v);
+        const unsigned long long key = (a << 32) | b;
+        const unsigned long long h1 = mix64(key ^ ((unsigned long long)(uint32_t)w * 0x9E3779B97F4A7C15ull));
+        const unsigned long long h2 = mix64((key + 0x632BE59BD9B4E019ull) ^ ((unsigned long long)(uint32_t)w << 17));
+        if (v < u) {
+          f1 += h1;
+          f2 += h2;
+        } else {
+          f1 -= h1;
+          f2 -= h2;
+        }
       }
-      if (!validate) continue;
-      if (u < 0 || u >= g.n) {
-        report(st, LC_ERR_ARG, v);
-        continue;
-      }
-      if (u == v) report(st, LC_ERR_SELF_LOOP, v);
-      if (e > vbeg && g.col[e - 1] >= u) report(st, LC_ERR_DUPLICATE, v);
-      if (w <= 0) report(st, LC_ERR_WEIGHT, v);
-      const unsigned long long a = (unsigned long long)(v < u ? v : u);
-      const unsigned long long b = (unsigned long long)(v < u ? u : v);
-      const unsigned long long key = (a << 32) | b;
-      const unsigned long long h1 = mix64(key ^ ((unsigned long long)(uint32_t)w * 0x9E3779B97F4A7C15ull));
-      const unsigned long long h2 = mix64((key + 0x632BE59BD9B4E019ull) ^ ((unsigned long long)(uint32_t)w << 17));
-      if (v < u) {
-        f1 += h1;
-        f2 += h2;
-      } else {
-        f1 -= h1;
-        f2 -= h2;
-      }
-    }
     }
     if (gid) graph_add(Tg, cur_g, tg);
   }
@@ -164,7 +194,12 @@ void launch_stats(const LevelGraph &g, int validate, GraphStats *st, const int32
     return (unsigned)b;
   };
   k_stats_vertices<<<blocks(g.n), 256, 0, s>>>(g, validate, st, gid, Vg, sw2g);
-  if (g.nnz > 0) k_stats_edges<<<blocks((g.nnz + 31) / 32), 256, 0, s>>>(g, validate, st, gid, Tg);
+  if (g.nnz > 0) {
+    const int64_t tiles = (g.nnz + kStatsTile - 1) / kStatsTile;
+    int64_t b = (tiles + kStatsThreads / 32 - 1) / (kStatsThreads / 32);
+    if (b > 152 * 6) b = 152 * 6;  // six blocks per SM (34 KB of shared memory each)
+    k_stats_edges<<<(unsigned)b, kStatsThreads, 0, s>>>(g, validate, st, gid, Tg);
+  }
 }
 
 void launch_labels_in_range(const int32_t *C, int64_t n, int64_t limit, GraphStats *st,

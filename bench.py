@@ -628,7 +628,7 @@ def main():
     ap.add_argument("--iterations", type=int, default=1,
                     help="iterated Louvain+ runs per step (single-graph workloads)")
     ap.add_argument("--requests", type=int, default=2000, help="requests per rate (served)")
-    ap.add_argument("--pool", type=int, default=64, help="distinct request graphs (served)")
+    ap.add_argument("--pool", type=int, default=256, help="distinct request graphs (served)")
     ap.add_argument("--rates", default="0.25,0.5,0.75,0.9,1.1",
                     help="arrival rates as fractions of the plain path's throughput (served)")
     ap.add_argument("--slots", type=int, default=4)

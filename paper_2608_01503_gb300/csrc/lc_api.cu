@@ -96,16 +96,34 @@ struct Prof {
   std::vector<Span> spans;
   int cur = -1;
   cudaEvent_t cur_a = nullptr;
+  // events are reused across calls (per thread and device), so a span's end
+  // costs one record and no event creation inside the span
+  static std::vector<cudaEvent_t> &pool() {
+    static thread_local std::vector<cudaEvent_t> p[16];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return p[dev & 15];
+  }
+  static cudaEvent_t take() {
+    auto &p = pool();
+    if (!p.empty()) {
+      cudaEvent_t e = p.back();
+      p.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
   void begin(int cls) {
     if (!on) return;
     cur = cls;
-    cudaEventCreate(&cur_a);
+    cur_a = take();
     cudaEventRecord(cur_a, s);
   }
   void end(double bytes) {
     if (!on) return;
-    cudaEvent_t b;
-    cudaEventCreate(&b);
+    cudaEvent_t b = take();
     cudaEventRecord(b, s);
     spans.push_back({cur, cur_a, b, bytes});
   }
@@ -116,8 +134,8 @@ struct Prof {
         res->kernel_ms[sp.cls] += ms;
         res->kernel_bytes[sp.cls] += sp.bytes;
       }
-      cudaEventDestroy(sp.a);
-      cudaEventDestroy(sp.b);
+      pool().push_back(sp.a);
+      pool().push_back(sp.b);
     }
     spans.clear();
   }

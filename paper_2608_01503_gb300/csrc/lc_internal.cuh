@@ -267,12 +267,21 @@ __device__ __forceinline__ bool better(long long g1, int32_t x1, long long g2, i
 }
 
 // floor(eps_den * delta / (eps_num * Lam)), the epsilon bucket of the
-// ordering of Section IV-A-1.
+// ordering of Section IV-A-1 (eps_num, eps_den, Lam > 0).  The products are
+// formed in 128 bits; when both fit in 64 bits, as they do unless delta or
+// Lam is near the exactness guards, one 64-bit division replaces the far
+// costlier 128-bit one.  Either way the quotient is exact.
 __device__ __forceinline__ long long eps_bucket(const Method &m, long long Lam, long long delta) {
-  __int128 num = (__int128)m.eps_den * delta;
-  __int128 den = (__int128)m.eps_num * Lam;
+  const __int128 num = (__int128)m.eps_den * delta;
+  const __int128 den = (__int128)m.eps_num * Lam;
+  if (num == (__int128)(long long)num && den == (__int128)(long long)den) {
+    const long long n64 = (long long)num, d64 = (long long)den;
+    long long q = n64 / d64;  // truncates toward zero
+    if (q * d64 != n64 && n64 < 0) q -= 1;
+    return q;
+  }
   __int128 qq = num / den;
-  if ((num % den) != 0 && num < 0) qq -= 1;
+  if (qq * den != num && num < 0) qq -= 1;
   return (long long)qq;
 }
 

@@ -331,6 +331,8 @@ def run_batched(args, rank, world):
     else:
         arms["default_graphs_on"] = lc.Options(graphs=True)
     main = "tuned" if tuning else "default"
+    if args.main_only:  # one arm (profiling captures)
+        arms = {main: arms[main]}
     # per-class breakdown from one profiled run of the main setting (not timed)
     opts_prof = lc.tuned_options(tuning, profile=True) if tuning else lc.Options(profile=True)
     for _ in range(args.warmup):
@@ -360,7 +362,7 @@ def run_batched(args, rank, world):
     clocks = sampler.stop()
     ms_step = arm_ms[main]
     # plain: one lc_cluster call per graph, every 16th graph (device-resident)
-    sample = graphs[::16]
+    sample = graphs[::16] if not args.no_plain else []
     dg = [(t(g.row_ptr), t(g.col), t(g.ew), t(g.vw), g.lam_num, g.lam_den) for g in sample]
     for x in dg[:4]:
         lc.lc_cluster(*x)
@@ -377,6 +379,7 @@ def run_batched(args, rank, world):
     torch.cuda.synchronize(dev)
     gp = b["graph_ptr"]
     same = all(torch.equal(labels[gp[16 * i]:gp[16 * i + 1]], plain_labels[i]) for i in range(len(sample)))
+    plain_gps = len(sample) / plain_s if sample else None
     nnz = int(b["col"].shape[0])
     if dist:  # stored edges of all ranks' graphs
         t_nnz = torch.tensor([nnz], dtype=torch.int64, device=dev)
@@ -394,9 +397,9 @@ def run_batched(args, rank, world):
             "edges_per_s": nnz / (ms_step / 1000.0),
             "arms_ms_per_step": arm_ms,
             "arms_graphs_per_s": {k: count / (v / 1000.0) for k, v in arm_ms.items()},
-            "plain": {"graphs_per_s": len(sample) / plain_s, "sample": f"every 16th graph ({len(sample)})",
-                      "identical_labels": bool(same)},
-            "speedup_vs_plain": value / (len(sample) / plain_s),
+            "plain": {"graphs_per_s": plain_gps, "sample": f"every 16th graph ({len(sample)})",
+                      "identical_labels": bool(same) if sample else None},
+            "speedup_vs_plain": value / plain_gps if plain_gps else None,
             "breakdown_ms_per_step": pres[0]["kernel_ms"],
             "clocks": clocks, "gpu_launches": int(klaunch)}
     if rank == 0:
@@ -638,6 +641,10 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="run lc_autotune on the workload first and cache its choice (tuning.json)")
     ap.add_argument("--no-tuning", action="store_true", help="ignore cached tunings")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batched: skip the one-call-per-graph comparison (profiling captures)")
+    ap.add_argument("--main-only", action="store_true",
+                    help="batched: time only the main launch settings (profiling captures)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

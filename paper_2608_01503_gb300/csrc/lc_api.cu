@@ -191,6 +191,7 @@ struct Run {
   // per graph
   long long *phi_acc = nullptr, *phi_out = nullptr, *phi_trace = nullptr;
   long long *obj = nullptr;  // [4 G] objective update after a call's last pass
+  long long *phi_final = nullptr;  // [G] Phi of C_out after each graph's last LocalMovePasses call
   long long *Tg = nullptr, *Vg = nullptr, *sw2g = nullptr;
   int *improved = nullptr;
   int32_t *gstart = nullptr;
@@ -237,6 +238,8 @@ static int alloc_per_graph(Run &r) {
   LC_TRY(r.ar.get(&r.phi_out, G));
   LC_TRY(r.ar.get(&r.phi_trace, G));
   LC_TRY(r.ar.get(&r.obj, 4 * (int64_t)G));
+  LC_TRY(r.ar.get(&r.phi_final, G));
+  LC_CK(cudaMemsetAsync(r.phi_final, 0, 8 * (size_t)G, r.s));  // a graph with no vertices: Phi = 0
   LC_TRY(r.ar.get(&r.Tg, G));
   LC_TRY(r.ar.get(&r.Vg, G));
   LC_TRY(r.ar.get(&r.sw2g, G));
@@ -321,7 +324,7 @@ static int resolve_plan(const lc_opts &o, BinPlan *out) {
 // upload_params, compact_level, contract_level), for the footprint below.
 static int64_t level0_scratch_bytes(int64_t n0, int64_t nnz0, int64_t G, int tables) {
   const int64_t n = n0 > 0 ? n0 : 1, big = 2 * nnz0 > n0 + 1 ? 2 * nnz0 : n0 + 1;
-  int64_t b = G * (10 * 8 + 4 + 4 + 1);                     // alloc_per_graph
+  int64_t b = G * (11 * 8 + 4 + 4 + 1);                     // alloc_per_graph
   b += 11 * 4 * n;                                           // C .. movers
   if (tables == 1) b += 2 * 4 * n + 8 * upd_list_size(n0, nnz0);
   b += 4 * scan_scratch(big);                                // scan32
@@ -672,6 +675,7 @@ static int local_move_passes(Run &r, Level &L, bool singleton, int level, int ph
         launch_objective(a, L.bins, r.s) + launch_graph_sums(a, r.s) + launch_bestof(a, r.C_out, r.s);
     r.prof.end(12.0 * nnz + 32.0 * n);
   }
+  r.res->kernel_launches[LC_K_OTHER] += launch_keep_phi(a, r.phi_final, r.s);
   LC_TRY(launch_check());
   if (r.o.event_cb && r.G == 1) {
     std::vector<int32_t> C(n > 0 ? n : 1);
@@ -1068,7 +1072,16 @@ static int cluster_impl(Run &r, const LevelGraph &g0, const std::vector<int64_t>
   LC_TRY(count_labels(r, L0, r.C_out, nc, &total));
   launch_relabel(r.C_out, r.newid, labels_out, L0.g.n, L0.gid, r.gstart, nullptr, 1, r.s);
   std::vector<long long> phi;
-  LC_TRY(objective_of(r, L0, r.C_out, phi));
+  if (r.o.uncoarsen && r.o.pass_limit >= 1 && !B0) {
+    // each graph's final clustering is the C_out of its last LocalMovePasses
+    // call, at level 0 (the uncoarsening call, or the coarsening call of a
+    // graph that stopped there), whose best-of test left its exact Phi
+    phi.assign(r.G, 0);
+    LC_CK(cudaMemcpyAsync(phi.data(), r.phi_final, 8 * (size_t)r.G, cudaMemcpyDeviceToHost, r.s));
+    LC_CK(cudaStreamSynchronize(r.s));
+  } else {
+    LC_TRY(objective_of(r, L0, r.C_out, phi));
+  }
   LC_TRY(check_device_error(r));
   for (int g = 0; g < r.G; ++g) {
     lc_result &res = r.res[g];

@@ -1945,6 +1945,17 @@ int launch_graph_sums(const PassArgs &a, cudaStream_t s) {
   return 1;
 }
 
+// phi_final[g] = phi_out[g] for the graphs that ran in this call.
+__global__ void k_keep_phi(const GraphParam *gp, const long long *phi_out, long long *phi_final, int G) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+    if (gp[g].active) phi_final[g] = phi_out[g];
+}
+
+int launch_keep_phi(const PassArgs &a, long long *phi_final, cudaStream_t s) {
+  k_keep_phi<<<blocks_for(a.G, 256), 256, 0, s>>>(a.gp, a.phi_out, phi_final, a.G);
+  return 1;
+}
+
 int launch_bestof(const PassArgs &a, int32_t *C_out, cudaStream_t s) {
   k_bestof_test<<<blocks_for(a.G, 256), 256, 0, s>>>(a.phi_acc, a.phi_out, a.improved, a.G);
   k_bestof_copy<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a, C_out);

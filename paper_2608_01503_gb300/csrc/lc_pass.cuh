@@ -122,6 +122,8 @@ int launch_apply(const PassArgs &a, const ApplyScratch &w, cudaStream_t s);
 int launch_graph_sums(const PassArgs &a, cudaStream_t s);
 // Per-graph best-of test and copy of improved graphs' labels into C_out.
 int launch_bestof(const PassArgs &a, int32_t *C_out, cudaStream_t s);
+// phi_final[g] = phi_out[g] for every graph active in the call (gp[g].active).
+int launch_keep_phi(const PassArgs &a, long long *phi_final, cudaStream_t s);
 void launch_iota(int32_t *C, int64_t n, cudaStream_t s);
 void launch_cluster_weights(const int32_t *C, const int64_t *vw, int64_t *W, int64_t n,
                             cudaStream_t s);

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(256, 4) k_move_thread(PassArgs a, const VRec *
 template <int G>
 __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const VRec *__restrict__ rec,
                                                     int64_t count) {
+  static_assert(G == 16 || G == 32, "the match key holds one group bit");
   __shared__ int32_t acc[256];
   long long cntL = 0, phi = 0, nX = 0;
   const int lane = threadIdx.x & 31;
@@ -221,8 +222,10 @@ __global__ void __launch_bounds__(256) k_move_small(PassArgs a, const VRec *__re
     const bool other = has && !self;
     const long long WX = other ? a.W[X] : 0;
     const long long S_self = group_sum<G>((long long)(self ? w : 0));
-    const unsigned long long key =
-        other ? (((unsigned long long)(lane / G) << 32) | (uint32_t)X) : (0xFFFFFFFF00000000ull | lane);
+    // 32-bit match key: the lane's group in bit 31 (G = 16) above the
+    // cluster id (< 2^31 - 1); lanes with nothing to add share the key
+    // 0xFFFFFFFF, which no (group, cluster) pair takes, and never add
+    const uint32_t key = other ? ((G < 32 ? (uint32_t)(lane / G) << 31 : 0u) | (uint32_t)X) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
     const int leader = __ffs(peers) - 1;
     acc[threadIdx.x] = 0;
@@ -612,8 +615,8 @@ __global__ void __launch_bounds__(kHubThreads) k_hub_move_insert(PassArgs a) {
     for (int k = 0; k < U; ++k) {
       const bool other = u[k] >= 0 && X[k] != Cv;
       if (u[k] >= 0 && X[k] == Cv) self += w[k];
-      const unsigned long long key =
-          other ? (unsigned long long)(uint32_t)X[k] : (0xFFFFFFFF00000000ull | lane);
+      // lanes with nothing to add share the key 0xFFFFFFFF (no cluster id)
+      const uint32_t key = other ? (uint32_t)X[k] : 0xFFFFFFFFu;
       const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
       const int leader = __ffs(peers) - 1;
       acc[threadIdx.x] = 0;

@@ -56,9 +56,11 @@ WORKLOADS = {
 
 
 # DRAM bytes per step of a kernel class, from one ncu capture (dram__bytes_read
-# + dram__bytes_write over every launch of the class) of the same kernels on
-# the same workload; a class whose kernels changed since has none (null).
-TRAFFIC_PER_STEP = {}
+# + dram__bytes_write over every launch of the class in one clustering) of the
+# same kernels on the same workload with the same launch settings ("tuned":
+# the cached lc_autotune choice); a class whose kernels changed since has none
+# (null).
+TRAFFIC_PER_STEP = {("rmat22", "move", "tuned"): 46_775_339_264}
 
 
 def make_graph(name: str, scale_override: int | None = None):
@@ -793,8 +795,9 @@ def main():
     achieved = kbytes[dom] / (kms[dom] / 1000.0) / 1e9 if kms[dom] > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (hbm_gbs)",
-                "traffic": (TRAFFIC_PER_STEP.get((args.workload, dom))
-                            if args.scale is None and K == 1 and args.method == "louvain+" else None),
+                "traffic": (TRAFFIC_PER_STEP.get((args.workload, dom, "tuned" if tuning else "default"))
+                            if args.scale is None and K == 1 and args.method == "louvain+" and args.tables == 0
+                            else None),
                 "traffic_unit": "DRAM bytes per step, all launches of the class (ncu)",
                 "launches": klaunch[dom],
                 "algorithmic_bytes_per_step": kbytes[dom] / args.steps,

@@ -170,7 +170,7 @@ typedef struct {
   int32_t ab_threads[5];    /* threads per candidate in the afterburner's launch groups
                                (bin 0, bin 1, bins 2-4, bins 5-6, bins 7-8): 0 = the
                                default (1, 16, 32, 128, 512); groups 2-4 also take 32, 128
-                               or 512.  Results do not depend on them. */
+                               or 512, group 2 also 16.  Results do not depend on them. */
   int32_t graphs;           /* 1 = the passes of a LocalMovePasses call that repeat the same
                                launches (all but a first pass from singletons and the last)
                                are captured once per call into a CUDA graph and replayed,

@@ -309,7 +309,8 @@ static int resolve_plan(const lc_opts &o, BinPlan *out) {
     const int32_t t = o.ab_threads[g];
     if (t == 0) continue;
     const bool fixed = g < 2 && t == p.ab_gs[g];  // bins 0 and 1 have one layout each
-    if (!fixed && !(g >= 2 && (t == 32 || t == 128 || t == 512))) return LC_ERR_ARG;
+    // group 2 (degrees up to 256 by default) may also take half a warp per candidate
+    if (!fixed && !(g >= 2 && (t == 32 || t == 128 || t == 512 || (g == 2 && t == 16)))) return LC_ERR_ARG;
     p.ab_gs[g] = t;
   }
   // kept tables share the shared-memory layout of the default bins (tab_cap)

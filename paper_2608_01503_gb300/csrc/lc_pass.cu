@@ -1673,6 +1673,7 @@ void set_ab_groups(PassArgs &a, const Bins &b, const BinPlan &plan) {
 
 // Groups 2-4: 32, 128 or 512 threads per candidate (BinPlan::ab_gs).
 static int launch_ab_wide_group(const PassArgs &a, const Bins &b, int g, cudaStream_t s) {
+  if (a.ab_gs[g] == 16) return launch_ab_group<16>(a, b, g, s);  // group 2 only
   if (a.ab_gs[g] == 32) return launch_ab_group<32>(a, b, g, s);
   if (a.ab_gs[g] == 128) return launch_ab_group<128>(a, b, g, s);
   return launch_ab_group<512>(a, b, g, s);

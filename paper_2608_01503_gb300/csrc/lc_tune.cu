@@ -146,9 +146,12 @@ extern "C" LC_API int lc_autotune(const lc_csr *g, const int64_t *vertex_w, cons
     c.bin_max_deg[k] = v;
     rc = try_setting(c);
   }
-  // 4. threads per candidate in the afterburner's wide groups
-  for (int g : {3, 4}) {
-    for (int t : {32, 128, 512}) {
+  // 4. threads per candidate in the afterburner's wide groups (group 2:
+  //    half a warp or a warp)
+  for (int g : {2, 3, 4}) {
+    for (int t : {16, 32, 128, 512}) {
+      if (g == 2 && t > 32) continue;
+      if (g > 2 && t == 16) continue;
       if (rc != LC_OK) break;
       lc_opts c = cur;
       if ((c.ab_threads[g] ? c.ab_threads[g] : kDefaultAb[g]) == t) continue;

@@ -340,6 +340,7 @@ BIN_PLANS = [
     dict(bins=(2, 3, 20, 100, 200, 300, 700, 1500, 3000), hub_chunk=256),
     dict(ab_threads=(0, 0, 128, 32, 32)),  # afterburner thread groups
     dict(ab_threads=(1, 16, 512, 512, 128), bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 2048)),
+    dict(ab_threads=(1, 16, 16, 32, 512)),  # half a warp per candidate in group 2
 ]
 
 
@@ -362,7 +363,7 @@ def test_invalid_bin_plans_rejected():
     for kw in (dict(bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 5000)),  # above bin 8's capacity
                dict(bins=(8, 16, 32, 128, 100)),  # decreasing
                dict(hub_chunk=100), dict(hub_chunk=1 << 20),
-               dict(ab_threads=(0, 0, 64)), dict(ab_threads=(32,)),
+               dict(ab_threads=(0, 0, 64)), dict(ab_threads=(32,)), dict(ab_threads=(0, 0, 0, 16)),
                dict(tables=1, bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 2048))):
         with pytest.raises(lc.LCError) as e:
             gpu_cluster(g, opts=lc.Options(**kw))

@@ -230,6 +230,13 @@ LC_API void lc_default_opts(lc_opts *o);
  * lc_result.scratch_peak_bytes).  -1 for negative sizes or count < 1. */
 LC_API int64_t lc_scratch_estimate(int64_t n, int64_t nnz, int32_t count, const lc_opts *opts);
 
+/* LC_OK if *opts is a valid option set for the clustering calls (pass limit
+ * and schedule, epsilon, symmetry and table modes, scratch limit, both or
+ * neither of alloc / dealloc, graphs, and the launch settings bin_max_deg /
+ * hub_chunk / ab_threads with their rules above), else LC_ERR_ARG; null
+ * opts: the defaults.  Host arithmetic only: needs no device. */
+LC_API int lc_check_opts(const lc_opts *opts);
+
 /* Launch settings chosen by lc_autotune. */
 typedef struct {
   int32_t bin_max_deg[9]; /* for lc_opts.bin_max_deg */

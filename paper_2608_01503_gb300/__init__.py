@@ -135,7 +135,7 @@ EXPORTS = ["lc_default_opts", "lc_strerror", "lc_cluster", "lc_cluster_batch", "
            "lc_contract", "lc_objective", "lc_objective_static", "lc_objective_static_max_vertices",
            "lc_server_default_config", "lc_server_create", "lc_server_submit", "lc_server_poll",
            "lc_server_wait", "lc_server_destroy", "lc_server_cancel", "lc_release_memory",
-           "lc_scratch_estimate", "lc_autotune", "lc_debug_enabled", "lc_debug_selftest"]
+           "lc_scratch_estimate", "lc_autotune", "lc_debug_enabled", "lc_debug_selftest", "lc_check_opts"]
 
 
 def library_path() -> str:
@@ -180,6 +180,8 @@ def load(build_if_missing: bool = True):
     lib.lc_scratch_estimate.restype = ctypes.c_int64
     lib.lc_autotune.argtypes = [csr, P, P, i32, P, P, P, opts, i32, ctypes.POINTER(_Tuning)]
     lib.lc_autotune.restype = ctypes.c_int
+    lib.lc_check_opts.argtypes = [opts]
+    lib.lc_check_opts.restype = ctypes.c_int
     lib.lc_debug_enabled.argtypes = []
     lib.lc_debug_enabled.restype = ctypes.c_int
     lib.lc_debug_selftest.argtypes = [P, ctypes.POINTER(i64)]
@@ -605,6 +607,13 @@ def save_tuning(key: str, tuning: dict, path: str = TUNING_CACHE) -> None:
 def lc_release_memory() -> None:
     """Returns the blocks cached in liblc's private pool on the current device."""
     _check(load().lc_release_memory())
+
+
+def lc_check_opts(opts: Options | None = None) -> None:
+    """Raises LCError (LC_ERR_ARG) if the options are not a valid set for the
+    clustering calls; host arithmetic only, no device needed."""
+    c = _c_opts(opts, None)
+    _check(load().lc_check_opts(ctypes.byref(c)))
 
 
 def lc_debug_enabled() -> bool:

@@ -1357,6 +1357,13 @@ void lc_default_opts(lc_opts *o) {
   o->event_ctx = nullptr;
 }
 
+int lc_check_opts(const lc_opts *opts) {
+  const lc_opts o = resolve_opts(opts);
+  LC_TRY(check_opts(o));
+  BinPlan p;
+  return resolve_plan(o, &p);
+}
+
 int64_t lc_scratch_estimate(int64_t n, int64_t nnz, int32_t count, const lc_opts *opts) {
   if (n < 0 || nnz < 0 || count < 1) return -1;
   return cluster_footprint(n, nnz, count, resolve_opts(opts));

@@ -143,3 +143,32 @@ def test_checked_build_compiles_and_exports_the_same_symbols():
     dbg = ctypes.CDLL(path)
     dbg.lc_debug_enabled.restype = ctypes.c_int
     assert dbg.lc_debug_enabled() == 1
+
+
+def test_option_sets_checked_on_the_host():
+    """lc_check_opts (host arithmetic, no device): the defaults and every
+    cached tuning are valid; malformed schedules, modes and launch settings
+    are refused with LC_ERR_ARG."""
+    import json
+
+    import paper_2608_01503_gb300 as lc
+
+    lc.lc_check_opts(None)
+    with open(lc.TUNING_CACHE) as f:
+        cache = json.load(f)
+    assert cache, "no cached tuning"
+    for key, tuning in cache.items():
+        lc.lc_check_opts(lc.tuned_options(tuning))
+        lc.lc_check_opts(lc.tuned_options(tuning, graphs=not tuning["graphs"]))
+    for kw in (dict(bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 5000)),  # above bin 8's capacity
+               dict(bins=(8, 16, 32, 128, 100)),  # decreasing
+               dict(hub_chunk=100), dict(hub_chunk=1 << 20),
+               dict(ab_threads=(0, 0, 64)), dict(ab_threads=(32,)), dict(ab_threads=(0, 0, 0, 16)),
+               dict(tables=1, bins=(8, 16, 32, 128, 256, 512, 1024, 2048, 2048)),
+               dict(pass_limit=17), dict(eps=(0, 10)), dict(phi=[(5, 4)]), dict(symmetry=3)):
+        with pytest.raises(lc.LCError) as e:
+            lc.lc_check_opts(lc.Options(**kw))
+        assert e.value.code == 1, kw
+    for kw in (dict(ab_threads=(1, 16, 16, 32, 512)), dict(bins=(8, 8, 8, 128, 128, 512, 512, 2048, 4096)),
+               dict(tables=1), dict(graphs=True, hub_chunk=4096)):
+        lc.lc_check_opts(lc.Options(**kw))

@@ -222,8 +222,9 @@ def run_reference(args, rank, world):
         sample = f"the first 8 requests of the served stream on {cores} host threads"
         unit = "graphs/s"
     elif args.workload == "rmat22":
-        graphs = [gg.rmat(21, 16, seed=1, wmax=8)]
-        sample = f"R-MAT scale 21 of the same recipe, OpenMP oracle on {cores} host cores"
+        graphs = [make_graph("rmat22", args.scale)]  # the benchmarked graph itself
+        sample = (f"the benchmarked R-MAT graph itself (scale {args.scale or 22}), "
+                  f"OpenMP oracle on {cores} host cores")
     elif args.workload == "grid256":
         graphs = [gg.grid_cpm(side=200)]
         sample = f"the 200^3 grid of the same recipe, OpenMP oracle on {cores} host cores"
@@ -256,7 +257,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]["desc"],
-                       "sample": sample, "nnz": sum(g.nnz for g in graphs)},
+                       "sample": sample, "nnz": sum(g.nnz for g in graphs),
+                       "same_config": args.workload in ("rmat22", "sbm10k")},
             "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
                              "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

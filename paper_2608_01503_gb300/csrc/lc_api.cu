@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -99,10 +100,10 @@ struct Prof {
   // events are reused across calls (per thread and device), so a span's end
   // costs one record and no event creation inside the span
   static std::vector<cudaEvent_t> &pool() {
-    static thread_local std::vector<cudaEvent_t> p[16];
+    static thread_local std::unordered_map<int, std::vector<cudaEvent_t>> p;  // by device
     int dev = 0;
     cudaGetDevice(&dev);
-    return p[dev & 15];
+    return p[dev];
   }
   static cudaEvent_t take() {
     auto &p = pool();

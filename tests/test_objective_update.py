@@ -92,3 +92,32 @@ def test_counting_rule_matters():
         if e["phi"] != phi0 + g.lam_den * d_twice - g.lam_num * dq:
             wrong += 1
     assert wrong > 0
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_result_objective_is_the_last_level0_call(seed):
+    """With uncoarsening, the reported objective equals the best-of value of
+    the last LocalMovePasses call at level 0 (the uncoarsening call, or the
+    coarsening call when the run stops at level 0), and its clustering is the
+    final one: the CUDA path reports that value instead of sweeping the graph
+    once more.  Without uncoarsening the final clustering is a projection, so
+    the identity is not used there."""
+    g = graph(seed)
+    labels, res, ev = oracle.louvain_plus(g, trace=True)
+    lmp0 = [e for e in ev if e["kind"] == "lmp" and e["level"] == 0]
+    assert lmp0
+    last = lmp0[-1]
+    assert last["phi"] == res["phi"] == oracle.objective(g, labels)
+    # same partition (labels are renumbered densely at the end)
+    _, a = np.unique(last["C"], return_inverse=True)
+    _, b = np.unique(labels, return_inverse=True)
+    pairs = set(zip(a.tolist(), b.tolist()))
+    assert len(pairs) == len(set(a.tolist())) == len(set(b.tolist()))
+
+
+def test_result_objective_on_larger_graphs():
+    for g in (gg.rmat(12, seed=2), gg.sbm_planted(n=3000, blocks=30, p_in=0.05, p_out=0.002, seed=6),
+              gg.grid_cpm(side=12)):
+        labels, res, ev = oracle.louvain_plus(g, trace=True)
+        last = [e for e in ev if e["kind"] == "lmp" and e["level"] == 0][-1]
+        assert last["phi"] == res["phi"] == oracle.objective(g, labels)

@@ -95,6 +95,20 @@ def test_heavy_weights_near_the_guards():
     check_full(gg.Graph(rp2, col2, ew2, vw2, 1, 1 << 24))
 
 
+def test_epsilon_bucket_beyond_64_bits():
+    """Settings inside the exactness guards where a product of the
+    afterburner's bucket leaves 64 bits, so the bucket takes its 128-bit
+    division: eps = 1 with eps_den = 2^31 - 1 on heavy weights (eps_den *
+    delta reaches 80 bits), and CPM with lambda = 2^-40 and eps_num =
+    2^31 - 1 (eps_num * Lambda reaches 71 bits).  Results still equal the
+    oracle's, whose bucket is always 128-bit."""
+    rp, col, ew = gg.rmat_csr(11, 8, 0.57, 0.19, 0.19, 5, 1, 1 << 15)
+    T = int(ew.astype(np.int64).sum())
+    check_full(gg.Graph(rp, col, ew, gg.weighted_degree(rp, ew), 1, T), lc.Options(eps=(2**31 - 1, 2**31 - 1)))
+    rp2, col2, ew2 = gg.random_graph(300, 0.05, 3, wmax=4)
+    check_full(gg.cpm_inputs(rp2, col2, ew2, 1, 2**40), lc.Options(eps=(2**31 - 1, 3)))
+
+
 @pytest.mark.parametrize("lam", [(0, 7), (7, 7), (1, 10**9)])
 def test_lambda_extremes(lam):
     rp, col, ew = gg.rmat_csr(12, 8, 0.57, 0.19, 0.19, 9, 1, 4)

@@ -73,3 +73,24 @@ def test_bench_percentile_helper():
     xs = [5, 1, 4, 2, 3]
     assert bench._pct(xs, 0.5) == 3 and bench._pct(xs, 0.99) == 5 and bench._pct([], 0.5) is None
     assert set(bench.ABLATIONS) >= {"default", "louvain", "phi0", "mlh_phi0", "no_symmetry_phi0"}
+
+
+def test_tuning_cache_round_trip(tmp_path):
+    """save_tuning / load_tuning keep one entry per workload and device, and
+    tuned_options carries every launch setting into the options (explicit
+    keywords win)."""
+    import paper_2608_01503_gb300 as lc
+
+    path = str(tmp_path / "tuning.json")
+    assert lc.load_tuning("rmat22/X", path) is None
+    t1 = {"bins": [8, 16, 32, 64, 256, 512, 1024, 2048, 4096], "hub_chunk": 4096,
+          "ab_threads": [1, 16, 16, 128, 128], "graphs": True, "ms_best": 1.0, "ms_default": 2.0, "trials": 3}
+    t2 = dict(t1, hub_chunk=2048, graphs=False)
+    lc.save_tuning("rmat22/X", t1, path)
+    lc.save_tuning("batched/X", t2, path)
+    assert lc.load_tuning("rmat22/X", path) == t1 and lc.load_tuning("batched/X", path) == t2
+    o = lc.tuned_options(t1, profile=True)
+    assert o.bins == tuple(t1["bins"]) and o.hub_chunk == 4096 and o.graphs is True
+    assert o.ab_threads == tuple(t1["ab_threads"]) and o.profile is True
+    assert lc.tuned_options(t1, graphs=False).graphs is False
+    assert lc.tuned_options(None) == lc.Options()
